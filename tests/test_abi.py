@@ -1,0 +1,64 @@
+"""The C ABI library loads and exports every function include/*.h declares
+(no GPU needed: nothing here launches work)."""
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DECL = re.compile(r"^\s*(?:const\s+)?(?:int|void|char|size_t|int32_t|uint32_t|gcm_status)\s*\**\s*(g(?:cm|fc)_\w+)\s*\(",
+                  re.M)
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        with open(h) as f:
+            names.update(DECL.findall(f.read()))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def native():
+    from paper_2602_23067_gb300 import build
+
+    build.build()
+    from paper_2602_23067_gb300 import _native
+
+    return _native
+
+
+def test_header_declares_the_core_calls():
+    names = declared_functions()
+    for n in ("gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "gcm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(native):
+    for name in declared_functions():
+        assert hasattr(native.lib, name), name
+
+
+def test_binding_covers_every_declared_symbol(native):
+    assert set(declared_functions()) <= set(native.SIGNATURES)
+
+
+def test_only_abi_symbols_are_exported(native):
+    out = subprocess.run(["nm", "-D", "--defined-only", native.LIB_PATH], capture_output=True, text=True).stdout
+    syms = [ln.split()[-1] for ln in out.splitlines() if ln.strip()]
+    exported = [s for s in syms if not s.startswith("_") and s not in ("_init", "_fini")]
+    assert exported, out
+    for s in exported:
+        assert s.startswith("gcm_") or s.startswith("gfc_"), s
+    assert not any("oracle" in s for s in syms)
+
+
+def test_errors_without_a_device_are_reported_not_raised(native):
+    # Argument checks run before any CUDA call.
+    import ctypes
+
+    rc = native.lib.gcm_encrypt(None, None, 16, None, 12, None, 0, None, 0, None, None, 0, None)
+    assert rc == native.GCM_ERR_INVALID_ARG
+    assert "NULL" in native.last_error()
