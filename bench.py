@@ -1,0 +1,423 @@
+#!/usr/bin/env python3
+"""Benchmark: AES-256-GCM on a 4 GiB FITS data unit on GB300.
+
+Workload: one synthetic FITS file, a 2880-byte header (36 cards, used as
+AAD) and the data unit of a 32768 x 32768 float32 image (N(1000, 50^2) sky
+plus Poisson point sources), zero-padded to whole 2880-byte records:
+4,294,969,920 bytes, generated on the device.  One step is the whole data
+path in both directions: GCM encryption of the data unit (key setup, fused
+CTR + GHASH map, tree combine and tag) followed by decrypt-verify (the same
+pass over the ciphertext, the tag check and the validation gate).
+
+    value = payload bytes processed (2 x data unit per step) / device time
+
+measured with CUDA events on the launching stream between a synchronised
+start and end; the inputs (4.3 GB) are far larger than the 129 MB L2, so no
+flush is needed between steps.  ``e2e`` is the same metric through the C ABI
+with pinned host buffers, host<->device copies inside the timed region.
+
+``--impl reference`` times the CPU oracle (plain byte-at-a-time AES-GCM) on a
+bounded prefix of the same data unit, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N1 = N2 = 32768
+DATA_BYTES = N1 * N2 * 4
+METRIC = "AES-GCM GB/s @4GiB on 1 GB300; batched p50/p99 latency vs per-msg launch"
+WORKLOAD = "fits_4gib_aes256gcm_enc+dec"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def workload_config(n_gpus):
+    from paper_2602_23067_gb300 import workloads
+
+    padded = workloads.padded_len(DATA_BYTES)
+    return {
+        "workload": WORKLOAD,
+        "cipher": "AES-256-GCM",
+        "iv_bits": 96,
+        "aad_bytes": 2880,
+        "payload_bytes": padded,
+        "image": "32768x32768 float32 BITPIX=-32, N(1000,50^2) + 10^4 Poisson point sources",
+        "step": "encrypt + decrypt-verify of the data unit",
+        "l2": "inputs (4.3 GB) exceed L2 (129 MB); no flush",
+        "per_gpu": "one 4 GiB message per GPU" if n_gpus > 1 else "one 4 GiB message",
+    }
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2602_23067_gb300", "csrc")
+    for name in ("gcm_kernels.cu", "gcm_device.cuh", "gcm_internal.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def load_traffic():
+    """DRAM bytes per fused-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "fused_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("source_sha256") == kernel_source_hash():
+            return float(d["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_oracle_sample(sample_bytes: int, seed: int = 2):
+    """Times the oracle (as it stands) on the first sample_bytes of the
+    workload's data unit, encrypt + decrypt-verify, one host thread."""
+    import numpy as np
+
+    import oracle
+    from paper_2602_23067_gb300 import workloads
+
+    r = workloads.rng(seed)
+    key = r.integers(0, 256, 32, dtype=np.uint8).tobytes()
+    iv = r.integers(0, 256, 12, dtype=np.uint8).tobytes()
+    header = workloads.fits_header(seed, -32, [N1, N2], ncards=36)
+    rows = max(1, sample_bytes // (N1 * 4))
+    pt = workloads.sky_image_host(seed, N1, rows, n_sources=5).tobytes()[:sample_bytes]
+    t0 = time.perf_counter()
+    ct, tag = oracle.gcm_encrypt(key, iv, header, pt)
+    ok, back = oracle.gcm_decrypt(key, iv, header, ct, tag)
+    dt = time.perf_counter() - t0
+    assert ok and back == pt
+    return 2 * len(pt), dt
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if n_gpus > 1 and world != n_gpus:
+        raise SystemExit("--gpus %d needs torchrun with %d processes" % (n_gpus, n_gpus))
+    return rank, local, world
+
+
+def run_reference(args):
+    rank, local, world = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    # Bound the run to about a minute of host work in total.
+    per_step = max(64 * 1024, min(4 << 20, int(60.0 / max(1, args.steps + args.warmup) * 1.5e6)))
+    per_step -= per_step % 16
+    for _ in range(args.warmup):
+        cpu_oracle_sample(per_step)
+    total_b, total_t = 0, 0.0
+    for _ in range(args.steps):
+        b, t = cpu_oracle_sample(per_step)
+        total_b += b
+        total_t += t
+    gbs = total_b / total_t / 1e9
+    sample = "first %d bytes of the 4 GiB data unit per step, header as AAD, encrypt + decrypt-verify" % per_step
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": gbs,
+        "unit": "GB/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_t / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": workload_config(args.gpus),
+        "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    rank, local, world = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import numpy as np
+
+    from paper_2602_23067_gb300 import Context, _native, workloads
+
+    padded = workloads.padded_len(DATA_BYTES)
+    seed = 2 + rank
+    r = workloads.rng(2)
+    key = r.integers(0, 256, 32, dtype=np.uint8).tobytes()
+    iv = r.integers(0, 256, 12, dtype=np.uint8).tobytes()
+    header = workloads.fits_header(2, -32, [N1, N2], ncards=36)
+    ctx = Context(local)
+    pt = torch.empty(padded, dtype=torch.uint8, device="cuda")
+    workloads.sky_image_device(seed, N1, N2, out=pt)
+    aad = torch.frombuffer(bytearray(header), dtype=torch.uint8).cuda()
+    ct = torch.empty_like(pt)
+    back = torch.empty_like(pt)
+    tag = torch.empty(16, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.encrypt_device(key, iv, aad, pt, ct=ct, tag=tag, stream=stream)
+        ctx.decrypt_verify_device(key, iv, aad, ct, tag, pt=back, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if not torch.equal(back, pt):
+        raise SystemExit("round trip mismatch")
+
+    # ---- device-resident timed region ----
+    _native.gcm_profile_enable(ctx.handle, True)
+    _native.gcm_profile_read(ctx.handle, reset=True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.25)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = _native.gcm_profile_read(ctx.handle, reset=True)
+    _native.gcm_profile_enable(ctx.handle, False)
+    if dist is not None:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bytes_per_step = 2 * padded
+    value = world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+
+    # ---- per-direction device throughput (secondary) ----
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.encrypt_device(key, iv, aad, pt, ct=ct, tag=tag, stream=stream)
+    e1.record(stream)
+    barrier()
+    enc_gbs = padded * args.steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.decrypt_verify_device(key, iv, aad, ct, tag, pt=back, stream=stream)
+    e1.record(stream)
+    barrier()
+    dec_gbs = padded * args.steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        del back
+        torch.cuda.empty_cache()
+        h_pt = torch.empty(padded, dtype=torch.uint8, pin_memory=True)
+        h_pt.copy_(pt)
+        h_ct = torch.empty_like(h_pt, pin_memory=True)
+        h_back = torch.empty_like(h_pt, pin_memory=True)
+        h_aad = np.frombuffer(header, dtype=np.uint8).copy()
+        ksteps = max(2, min(args.steps, 8))
+
+        def host_step():
+            _, t = ctx.encrypt_host(key, iv, h_aad, h_pt, ct=h_ct)
+            ctx.decrypt_verify_host(key, iv, h_aad, h_ct, t, pt=h_back)
+
+        host_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            host_step()
+        barrier()
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        if not torch.equal(h_back, h_pt):
+            raise SystemExit("host round trip mismatch")
+        e2e = {
+            "value": world * bytes_per_step * ksteps / dt / 1e9,
+            "unit": "GB/s",
+            "h2d_bytes_per_step": (2880 + padded) + (2880 + padded + 16),
+            "d2h_bytes_per_step": (padded + 16) + (padded + 4),
+            "steps": ksteps,
+            "api": "gcm_encrypt + gcm_decrypt_verify, GCM_MEM_HOST, pinned buffers",
+        }
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (the fused CTR+GHASH map) ----
+    peak, peak_kind = load_peaks()
+    kern_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    kern_bytes = prof["fused_bytes"] / max(1, prof["fused_launches"])
+    achieved = kern_bytes / (kern_ms * 1e-3) / 1e9
+    roofline = {
+        "bound": "hbm",
+        "achieved": achieved,
+        "peak": peak,
+        "unit": "GB/s",
+        "frac": achieved / peak,
+        "traffic": load_traffic(),
+        "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured"
+        else "fallback 6.8 TB/s",
+        "kernel": "fused_kernel<14> (AES-256 CTR + GHASH map)",
+        "algorithmic_bytes_per_launch": kern_bytes,
+        "avg_launch_ms": kern_ms,
+    }
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        nb, dt = cpu_oracle_sample(args.cpu_sample_bytes)
+        cpu = {"value": nb / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "first %d bytes of the data unit, header as AAD, AES-256-GCM encrypt + decrypt-verify, "
+                         "single host thread (%.1f s)" % (args.cpu_sample_bytes, dt)}
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": workload_config(world),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+        "directions": {"encrypt_gbs": enc_gbs, "decrypt_verify_gbs": dec_gbs},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-bytes", type=int, default=8 << 20)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,134 @@
+/*
+ * gcmgpu.h -- C ABI of the GB300 AES-GCM library.
+ *
+ * The library implements AES-GCM authenticated encryption and decryption
+ * (NIST SP 800-38D over the FIPS-197 block cipher) as adopted by the paper
+ * "GpuFitsCrypt" (Sec. 3.2.1): the AES-CTR keystream fused, in one pass over
+ * the data, with GHASH recast as the paper's parallel reduction (Sec. 3.3.1,
+ * Eq. 1 and Fig. 2b; Sec. 5.2.1-5.2.3): per-chunk Horner, a device table of
+ * powers of H, and a log-depth combination of chunk partials.  The session
+ * object mirrors the paper's context API (Table "Core functions",
+ * gfc_context_create / gfc_context_destroy) and the FITS entry points follow
+ * its FitsOperationResult convention (same table).
+ *
+ * Conventions that hold for every call below:
+ *   - Every function returns a gcm_status (0 = success, negative = error).
+ *     The message of the last error on the calling thread is available
+ *     from gcm_last_error().
+ *   - key and iv are always HOST pointers; the library copies them.
+ *   - Buffers named "data" (aad, pt, ct, tag) are DEVICE pointers when
+ *     mem == GCM_MEM_DEVICE and HOST pointers when mem == GCM_MEM_HOST.
+ *     Device data buffers for pt/ct must be 16-byte aligned; aad and tag
+ *     buffers have no alignment requirement.
+ *   - The caller owns all buffers it passes.  ct may equal pt (in place).
+ *   - stream is a cudaStream_t (NULL = the legacy default stream).  Device
+ *     mode encryption is asynchronous on that stream; the tag is valid once
+ *     the stream reaches the point of the call.
+ *   - A length of zero is valid for aad and for the payload.  A NULL
+ *     pointer is accepted only together with a zero length.
+ *   - Limits (SP 800-38D sec. 5.2.1.1): payload <= 2^36 - 32 bytes, aad <=
+ *     2^61 - 1 bytes.  IVs must be 1..65536 bytes (the standard allows
+ *     longer IVs; this library caps them and reports GCM_ERR_LENGTH_LIMIT).
+ */
+#ifndef GCMGPU_H
+#define GCMGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- */
+/* Status codes (the paper's convention: 0 success, < 0 error;      */
+/* Table "Core functions", error_code row)                          */
+/* ---------------------------------------------------------------- */
+typedef enum {
+    GCM_OK = 0,
+    GCM_ERR_INVALID_ARG = -1,   /* bad key/IV length, NULL with nonzero length, bad mode */
+    GCM_ERR_LENGTH_LIMIT = -2,  /* payload, AAD or IV beyond the limits above */
+    GCM_ERR_AUTH = -3,          /* tag mismatch: the output was zero-filled (Sec. 4.2) */
+    GCM_ERR_NO_MEMORY = -4,     /* device/pinned allocation failed or HBM budget exceeded */
+    GCM_ERR_CUDA = -5,          /* a CUDA runtime call failed */
+    GCM_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
+    GCM_ERR_ALIGNMENT = -7,     /* a device pt/ct pointer is not 16-byte aligned */
+    GCM_ERR_BUSY = -8           /* serving queue full; retry later */
+} gcm_status;
+
+/* Where the data buffers of a call live. */
+typedef enum {
+    GCM_MEM_DEVICE = 0,
+    GCM_MEM_HOST = 1
+} gcm_mem;
+
+/* Opaque session: device scratch pools, streams, the key cache and the HBM
+ * budget.  One context serves one device. */
+typedef struct gcm_ctx gcm_ctx;
+
+/* Creates a session on CUDA device `device`.  hbm_budget_bytes caps the
+ * device scratch the session may hold (0 = no cap).  Builds the AES round
+ * tables on the device.  *out receives the context; it is NULL on error.
+ * Mirrors gfc_context_create (Table "Core functions"). */
+int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes);
+
+/* Releases every device and host resource of the session (mirrors
+ * gfc_context_destroy).  Waits for the session's own streams.  NULL is a
+ * no-op. */
+void gcm_ctx_destroy(gcm_ctx *ctx);
+
+/* Message of the last error seen on the calling thread ("" if none). */
+const char *gcm_last_error(void);
+
+/* GCM-AE (SP 800-38D Algorithm 4; the paper's AES-GCM, Sec. 3.2.1).
+ *   key/key_len : 16 or 32 bytes (AES-128 / AES-256), 24 (AES-192) also works.
+ *   iv/iv_len   : 12 bytes is the fast path J0 = IV || 0^31 || 1; any other
+ *                 length uses J0 = GHASH(IV || pad || [len(IV)]_64).
+ *   aad/aad_len : additional authenticated data (e.g. a FITS header).
+ *   pt/len      : plaintext;  ct receives len bytes of ciphertext.
+ *   tag         : receives the 16-byte tag T = E_K(J0) xor GHASH_H(A, C).
+ * Device mode: returns once the work is enqueued on `stream`.
+ * Host mode:   copies through device scratch and returns when done. */
+int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+                const uint8_t *iv, size_t iv_len,
+                const uint8_t *aad, size_t aad_len,
+                const uint8_t *pt, size_t len, uint8_t *ct, uint8_t *tag,
+                int mem, void *stream);
+
+/* GCM-AD (SP 800-38D Algorithm 5) with the paper's validation gate
+ * (Sec. 3.3.2 item 4): the GHASH is taken over the input ciphertext in the
+ * same pass that writes the plaintext; the tag is then compared in constant
+ * time and, on a mismatch, the plaintext buffer is zero-filled on the device
+ * (the payload suppression of Sec. 4.2) before the call returns
+ * GCM_ERR_AUTH.  The call synchronises `stream` to read the verdict.
+ * `tag` holds the 16 expected tag bytes (a device pointer in device mode). */
+int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+                       const uint8_t *iv, size_t iv_len,
+                       const uint8_t *aad, size_t aad_len,
+                       const uint8_t *ct, size_t len, const uint8_t *tag,
+                       uint8_t *pt, int mem, void *stream);
+
+/* ---------------------------------------------------------------- */
+/* Measurement hooks (used by the benchmark; no counterpart in the  */
+/* paper beyond its cudaEventRecord protocol, Sec. 5.3.1)           */
+/* ---------------------------------------------------------------- */
+
+/* When enabled, every launch of the fused CTR+GHASH kernel is bracketed by
+ * CUDA events recorded on the stream it is launched on, and every kernel the
+ * library launches is counted.  Costs two event records per call. */
+int gcm_profile_enable(gcm_ctx *ctx, int enable);
+
+/* Waits for the recorded events and returns, since the last reset:
+ * fused_ms: summed device time of the fused kernel launches;
+ * fused_launches: their number; fused_bytes: algorithmic bytes they moved
+ * (payload read + payload written + AAD read); launches: all kernels
+ * launched by the library.  Any output pointer may be NULL.  reset != 0
+ * clears the totals afterwards. */
+int gcm_profile_read(gcm_ctx *ctx, int reset, double *fused_ms, uint64_t *fused_launches,
+                     uint64_t *fused_bytes, uint64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GCMGPU_H */

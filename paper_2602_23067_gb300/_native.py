@@ -1,0 +1,123 @@
+"""ctypes binding of ``libgcmgpu.so`` (the C ABI in ``include/gcmgpu.h``).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  If the library has not been built, importing this module
+raises; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgcmgpu.so")
+
+GCM_OK = 0
+GCM_ERR_INVALID_ARG = -1
+GCM_ERR_LENGTH_LIMIT = -2
+GCM_ERR_AUTH = -3
+GCM_ERR_NO_MEMORY = -4
+GCM_ERR_CUDA = -5
+GCM_ERR_TIMEOUT = -6
+GCM_ERR_ALIGNMENT = -7
+GCM_ERR_BUSY = -8
+
+GCM_MEM_DEVICE = 0
+GCM_MEM_HOST = 1
+
+STATUS_NAMES = {
+    GCM_OK: "GCM_OK",
+    GCM_ERR_INVALID_ARG: "GCM_ERR_INVALID_ARG",
+    GCM_ERR_LENGTH_LIMIT: "GCM_ERR_LENGTH_LIMIT",
+    GCM_ERR_AUTH: "GCM_ERR_AUTH",
+    GCM_ERR_NO_MEMORY: "GCM_ERR_NO_MEMORY",
+    GCM_ERR_CUDA: "GCM_ERR_CUDA",
+    GCM_ERR_TIMEOUT: "GCM_ERR_TIMEOUT",
+    GCM_ERR_ALIGNMENT: "GCM_ERR_ALIGNMENT",
+    GCM_ERR_BUSY: "GCM_ERR_BUSY",
+}
+
+# Every symbol the header declares, with its ctypes signature.
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+SIGNATURES = {
+    "gcm_ctx_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _SZ]),
+    "gcm_ctx_destroy": (None, [_VP]),
+    "gcm_last_error": (ctypes.c_char_p, []),
+    "gcm_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, _VP]),
+    "gcm_decrypt_verify": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, _VP]),
+    "gcm_profile_enable": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "gcm_profile_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+}
+
+
+class GcmError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__("%s (%d): %s" % (STATUS_NAMES.get(code, "?"), code, message))
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            "libgcmgpu.so is not built (expected at %s); run "
+            "`python -c 'import __graft_entry__ as g; g.build()'` first" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def last_error() -> str:
+    msg = lib.gcm_last_error()
+    return msg.decode("utf-8", "replace") if msg else ""
+
+
+def check(rc: int) -> int:
+    if rc != GCM_OK:
+        raise GcmError(rc, last_error())
+    return rc
+
+
+def gcm_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
+    h = _VP()
+    check(lib.gcm_ctx_create(ctypes.byref(h), device, hbm_budget_bytes))
+    return h.value
+
+
+def gcm_ctx_destroy(ctx: Optional[int]) -> None:
+    lib.gcm_ctx_destroy(ctx)
+
+
+def gcm_encrypt(ctx, key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, pt_ptr, length, ct_ptr, tag_ptr,
+                mem, stream) -> int:
+    """Raw call: pointers are integers (host or device per ``mem``).  Returns
+    the status code without raising."""
+    return lib.gcm_encrypt(ctx, key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, pt_ptr, length,
+                           ct_ptr, tag_ptr, mem, stream)
+
+
+def gcm_decrypt_verify(ctx, key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, ct_ptr, length, tag_ptr,
+                       pt_ptr, mem, stream) -> int:
+    return lib.gcm_decrypt_verify(ctx, key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, ct_ptr, length,
+                                  tag_ptr, pt_ptr, mem, stream)
+
+
+def gcm_profile_enable(ctx, enable: bool) -> None:
+    check(lib.gcm_profile_enable(ctx, 1 if enable else 0))
+
+
+def gcm_profile_read(ctx, reset: bool = False):
+    """Returns dict(fused_ms, fused_launches, fused_bytes, launches)."""
+    ms, nl, nb, la = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib.gcm_profile_read(ctx, 1 if reset else 0, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nb),
+                               ctypes.byref(la)))
+    return {"fused_ms": ms.value, "fused_launches": nl.value, "fused_bytes": nb.value, "launches": la.value}

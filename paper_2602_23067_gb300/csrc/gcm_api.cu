@@ -1,0 +1,467 @@
+// gcm_api.cu -- C ABI of the library (declared in include/gcmgpu.h).
+//
+// Host code only validates arguments, sizes the tiling, takes per-call device
+// scratch from a stream-ordered pool and enqueues the kernels of
+// gcm_kernels.cu.  Every step of the method runs on the device.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "gcm_internal.h"
+#include "gcmgpu.h"
+
+using namespace gcmgpu;
+
+struct gcm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;          // 0 = unlimited
+    size_t in_flight = 0;       // scratch bytes held by calls not yet returned
+    cudaMemPool_t pool = nullptr;
+    DevTables *tabs = nullptr;
+    std::mutex mu;
+    // measurement hooks
+    std::atomic<int> profiling{0};
+    std::atomic<uint64_t> launches{0};
+    struct Timed {
+        cudaEvent_t start, stop;
+        uint64_t bytes;
+    };
+    std::vector<Timed> timed;       // recorded, not yet read
+    std::vector<cudaEvent_t> spare; // recycled events
+    double fused_ms = 0.0;
+    uint64_t fused_launches = 0, fused_bytes = 0;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, const char *detail = nullptr)
+{
+    char buf[512];
+    if (detail)
+        snprintf(buf, sizeof(buf), fmt, detail);
+    else
+        snprintf(buf, sizeof(buf), "%s", fmt);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    g_last_error = buf;
+    return GCM_ERR_CUDA;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr uint64_t MAX_PAYLOAD = (1ull << 36) - 32;  // 2^39 - 256 bits
+constexpr uint64_t MAX_AAD = (1ull << 61) - 1;       // 2^64 - 1 bits
+constexpr uint64_t MAX_IV = 65536;                    // library cap
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+cudaEvent_t take_event(gcm_ctx *ctx)
+{
+    // caller holds ctx->mu
+    if (!ctx->spare.empty()) {
+        cudaEvent_t e = ctx->spare.back();
+        ctx->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Tile size: 2^16 blocks (1 MiB) for large sequences; smaller for short ones
+// so that there are at least a few tiles per SM.
+uint32_t choose_tile_log2(uint64_t M, int num_sms)
+{
+    uint32_t lg = 16;
+    while (lg > 10 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
+    return lg;
+}
+
+struct Scratch {
+    void *base = nullptr;
+    size_t bytes = 0;
+};
+
+int scratch_alloc(gcm_ctx *ctx, size_t bytes, cudaStream_t s, Scratch &out)
+{
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (ctx->budget && ctx->in_flight + bytes > ctx->budget)
+            return fail(GCM_ERR_NO_MEMORY, "device scratch would exceed the context's HBM budget");
+        ctx->in_flight += bytes;
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(&out.base, bytes, ctx->pool, s);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->in_flight -= bytes;
+        cudaGetLastError();
+        return fail(GCM_ERR_NO_MEMORY, "device scratch allocation failed: %s", cudaGetErrorString(e));
+    }
+    out.bytes = bytes;
+    return GCM_OK;
+}
+
+void scratch_free(gcm_ctx *ctx, Scratch &sc, cudaStream_t s)
+{
+    if (sc.base) cudaFreeAsync(sc.base, s);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->in_flight -= sc.bytes;
+    sc.base = nullptr;
+    sc.bytes = 0;
+}
+
+int check_common(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                 const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, const uint8_t *out,
+                 const uint8_t *tag, int mem)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (mem != GCM_MEM_DEVICE && mem != GCM_MEM_HOST) return fail(GCM_ERR_INVALID_ARG, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");
+    if (!key || (key_len != 16 && key_len != 24 && key_len != 32))
+        return fail(GCM_ERR_INVALID_ARG, "key must be 16, 24 or 32 bytes");
+    if (!iv || iv_len == 0) return fail(GCM_ERR_INVALID_ARG, "IV must be at least one byte");
+    if (iv_len > MAX_IV) return fail(GCM_ERR_LENGTH_LIMIT, "IV longer than 65536 bytes");
+    if (len > MAX_PAYLOAD) return fail(GCM_ERR_LENGTH_LIMIT, "payload longer than 2^36 - 32 bytes");
+    if ((uint64_t)aad_len > MAX_AAD) return fail(GCM_ERR_LENGTH_LIMIT, "AAD longer than 2^61 - 1 bytes");
+    if (aad_len && !aad) return fail(GCM_ERR_INVALID_ARG, "aad is NULL with a nonzero length");
+    if (len && (!in || !out)) return fail(GCM_ERR_INVALID_ARG, "payload pointer is NULL with a nonzero length");
+    if (!tag) return fail(GCM_ERR_INVALID_ARG, "tag pointer is NULL");
+    if (mem == GCM_MEM_DEVICE && len &&
+        (((uintptr_t)in & 15u) != 0 || ((uintptr_t)out & 15u) != 0))
+        return fail(GCM_ERR_ALIGNMENT, "device payload pointers must be 16-byte aligned");
+    return GCM_OK;
+}
+
+// Enqueues the whole device path for one message whose aad/in/out/tag live
+// in device memory.  For decryption `tag_dev` is the expected tag and
+// `status_dev` receives 0 or GCM_ERR_AUTH; for encryption the tag is written.
+int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                   const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out,
+                   uint8_t *tag_dev, bool decrypt, int32_t *status_dev, Scratch &sc, cudaStream_t s)
+{
+    const uint64_t a_blocks = (aad_len + 15) / 16;
+    const uint64_t n_blocks = (len + 15) / 16;
+    const uint64_t M = a_blocks + n_blocks;
+    const uint32_t lg = choose_tile_log2(M, ctx->num_sms);
+    const uint64_t K = (M + (1ull << lg) - 1) >> lg;
+    uint32_t levels = 0;
+    while ((1ull << levels) < K) levels++;
+    if (lg + levels >= (uint32_t)H2K_COUNT) return fail(GCM_ERR_LENGTH_LIMIT, "message too long for the power table");
+
+    // Scratch layout: KeyMat | MsgMat | partials[K] | tree scratch | IV copy
+    const size_t off_km = 0;
+    const size_t off_mm = align_up(off_km + sizeof(KeyMat), 256);
+    const size_t off_part = align_up(off_mm + sizeof(MsgMat), 256);
+    const size_t off_tree = align_up(off_part + (size_t)K * sizeof(gf128), 256);
+    const size_t off_iv = align_up(off_tree + (size_t)(K / 2 + 1) * sizeof(gf128), 256);
+    const size_t total = align_up(off_iv + (iv_len > IV_INLINE_MAX ? iv_len : 0), 256);
+    int rc = scratch_alloc(ctx, total, s, sc);
+    if (rc) return rc;
+    uint8_t *base = static_cast<uint8_t *>(sc.base);
+    KeyMat *km = reinterpret_cast<KeyMat *>(base + off_km);
+    MsgMat *mm = reinterpret_cast<MsgMat *>(base + off_mm);
+    gf128 *partials = reinterpret_cast<gf128 *>(base + off_part);
+    gf128 *tree = reinterpret_cast<gf128 *>(base + off_tree);
+
+    KsParams ks;
+    memset(&ks, 0, sizeof(ks));
+    memcpy(ks.key, key, key_len);
+    ks.key_len = (uint32_t)key_len;
+    ks.iv_len = (uint32_t)iv_len;
+    if (iv_len <= IV_INLINE_MAX) {
+        memcpy(ks.iv_inline, iv, iv_len);
+    } else {
+        uint8_t *div = base + off_iv;
+        cudaError_t e = cudaMemcpyAsync(div, iv, iv_len, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "IV copy");
+        ks.iv_dev = div;
+    }
+    ks.km = km;
+    ks.mm = mm;
+    ks.tabs = ctx->tabs;
+    cudaError_t e = launch_key_setup(ks, s);
+    if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
+    ctx->launches += 1;
+
+    const int nr = (int)key_len / 4 + 6;
+    KfParams kf;
+    memset(&kf, 0, sizeof(kf));
+    kf.in = in;
+    kf.out = out;
+    kf.aad = aad;
+    kf.len = len;
+    kf.aad_len = aad_len;
+    kf.a_blocks = a_blocks;
+    kf.n_full = len / 16;
+    kf.M = M;
+    kf.K = K;
+    kf.tile_log2 = lg;
+    kf.decrypt = decrypt ? 1u : 0u;
+    kf.km = km;
+    kf.mm = mm;
+    kf.tabs = ctx->tabs;
+    kf.partials = partials;
+    const int grid = (int)((K < (uint64_t)ctx->num_sms) ? K : (uint64_t)ctx->num_sms);
+    const bool prof = ctx->profiling.load() != 0 && K > 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (prof) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ev0 = take_event(ctx);
+        ev1 = take_event(ctx);
+    }
+    if (prof) cudaEventRecord(ev0, s);
+    e = launch_fused(kf, nr, grid, s);
+    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+    if (prof) {
+        cudaEventRecord(ev1, s);
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->timed.push_back({ev0, ev1, (uint64_t)len * 2u + (uint64_t)aad_len});
+    }
+    ctx->launches += (K > 0) ? 1 : 0;
+
+    KcParams kc;
+    memset(&kc, 0, sizeof(kc));
+    kc.partials = partials;
+    kc.scratch = tree;
+    kc.K = K;
+    kc.tile_log2 = lg;
+    kc.aad_len = aad_len;
+    kc.len = len;
+    kc.km = km;
+    kc.mm = mm;
+    kc.tag_out = decrypt ? nullptr : tag_dev;
+    kc.tag_expected = decrypt ? tag_dev : nullptr;
+    kc.status = status_dev;
+    e = launch_combine(kc, s);
+    if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
+    ctx->launches += 1;
+
+    if (decrypt && len) {
+        KzParams kz;
+        kz.out = out;
+        kz.len = len;
+        kz.status = status_dev;
+        const uint64_t nvec = len / 16 + 1;
+        uint64_t g = (nvec + 255) / 256;
+        if (g > (uint64_t)ctx->num_sms * 8) g = (uint64_t)ctx->num_sms * 8;
+        e = launch_zero_on_fail(kz, (int)g, s);
+        if (e != cudaSuccess) return cuda_fail(e, "zero-fill launch");
+        ctx->launches += 1;
+    }
+    return GCM_OK;
+}
+
+int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+             const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out, uint8_t *tag,
+             bool decrypt, int mem, void *stream)
+{
+    int rc = check_common(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, tag, mem);
+    if (rc) return rc;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+    // Per-call device buffers: status word, and in host mode the staged data.
+    const bool host = (mem == GCM_MEM_HOST);
+    const size_t off_status = 0;
+    const size_t off_tag = 256;
+    const size_t off_aad = 512;
+    const size_t off_data = align_up(off_aad + (host ? aad_len : 0), 256);
+    const size_t total = align_up(off_data + (host ? len : 0), 256);
+    Scratch io;
+    rc = scratch_alloc(ctx, total, s, io);
+    if (rc) return rc;
+    uint8_t *iob = static_cast<uint8_t *>(io.base);
+    int32_t *d_status = reinterpret_cast<int32_t *>(iob + off_status);
+    uint8_t *d_tag = host ? iob + off_tag : tag;
+    const uint8_t *d_aad = host ? iob + off_aad : aad;
+    uint8_t *d_data = host ? iob + off_data : nullptr;
+    const uint8_t *d_in = host ? d_data : in;
+    uint8_t *d_out = host ? d_data : out;
+    cudaError_t e = cudaSuccess;
+
+    if (host) {
+        if (aad_len) e = cudaMemcpyAsync(iob + off_aad, aad, aad_len, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && len) e = cudaMemcpyAsync(d_data, in, len, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && decrypt) e = cudaMemcpyAsync(d_tag, tag, 16, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            scratch_free(ctx, io, s);
+            return cuda_fail(e, "host-to-device copy");
+        }
+    }
+
+    Scratch sc;
+    rc = enqueue_device(ctx, key, key_len, iv, iv_len, d_aad, aad_len, d_in, len, d_out, d_tag, decrypt,
+                        d_status, sc, s);
+    if (rc) {
+        if (sc.base) scratch_free(ctx, sc, s);
+        scratch_free(ctx, io, s);
+        return rc;
+    }
+    scratch_free(ctx, sc, s);
+
+    if (host) {
+        if (len) e = cudaMemcpyAsync(out, d_data, len, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && !decrypt) e = cudaMemcpyAsync(tag, d_tag, 16, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) {
+            scratch_free(ctx, io, s);
+            return cuda_fail(e, "device-to-host copy");
+        }
+    }
+    int32_t status = 0;
+    if (decrypt) {
+        e = cudaMemcpyAsync(&status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    } else if (host) {
+        e = cudaStreamSynchronize(s);
+    }
+    scratch_free(ctx, io, s);
+    if (e != cudaSuccess) return cuda_fail(e, "synchronisation");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "asynchronous kernel error");
+    if (decrypt && status != 0) return fail(GCM_ERR_AUTH, "authentication tag mismatch: output zero-filled");
+    return GCM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gcm_last_error(void) { return g_last_error.c_str(); }
+
+int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
+{
+    if (!out) return fail(GCM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(GCM_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the device");
+    gcm_ctx *ctx = new gcm_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes;
+    e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = configure_kernels();
+    if (e == cudaSuccess) {
+        cudaMemPoolProps props;
+        memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        e = cudaMemPoolCreate(&ctx->pool, &props);
+    }
+    if (e == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;  // keep freed scratch cached for later calls
+        e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tabs, sizeof(DevTables));
+    if (e == cudaSuccess) e = launch_build_tables(ctx->tabs, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "context creation");
+        gcm_ctx_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return GCM_OK;
+}
+
+int gcm_profile_enable(gcm_ctx *ctx, int enable)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    ctx->profiling = enable ? 1 : 0;
+    return GCM_OK;
+}
+
+int gcm_profile_read(gcm_ctx *ctx, int reset, double *fused_ms, uint64_t *fused_launches,
+                     uint64_t *fused_bytes, uint64_t *launches)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    DeviceGuard guard(ctx->device);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (auto &t : ctx->timed) {
+        cudaError_t e = cudaEventSynchronize(t.stop);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.start, t.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "reading profile events");
+        ctx->fused_ms += ms;
+        ctx->fused_launches += 1;
+        ctx->fused_bytes += t.bytes;
+        ctx->spare.push_back(t.start);
+        ctx->spare.push_back(t.stop);
+    }
+    ctx->timed.clear();
+    if (fused_ms) *fused_ms = ctx->fused_ms;
+    if (fused_launches) *fused_launches = ctx->fused_launches;
+    if (fused_bytes) *fused_bytes = ctx->fused_bytes;
+    if (launches) *launches = ctx->launches.load();
+    if (reset) {
+        ctx->fused_ms = 0.0;
+        ctx->fused_launches = 0;
+        ctx->fused_bytes = 0;
+        ctx->launches = 0;
+    }
+    return GCM_OK;
+}
+
+void gcm_ctx_destroy(gcm_ctx *ctx)
+{
+    if (!ctx) return;
+    {
+        DeviceGuard guard(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &t : ctx->timed) {
+            cudaEventDestroy(t.start);
+            cudaEventDestroy(t.stop);
+        }
+        for (auto e : ctx->spare) cudaEventDestroy(e);
+        if (ctx->tabs) cudaFree(ctx->tabs);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    }
+    delete ctx;
+}
+
+int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                const uint8_t *aad, size_t aad_len, const uint8_t *pt, size_t len, uint8_t *ct, uint8_t *tag,
+                int mem, void *stream)
+{
+    return run_call(ctx, key, key_len, iv, iv_len, aad, aad_len, pt, len, ct, tag, false, mem, stream);
+}
+
+int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                       const uint8_t *aad, size_t aad_len, const uint8_t *ct, size_t len, const uint8_t *tag,
+                       uint8_t *pt, int mem, void *stream)
+{
+    return run_call(ctx, key, key_len, iv, iv_len, aad, aad_len, ct, len, pt, const_cast<uint8_t *>(tag), true,
+                    mem, stream);
+}
+
+}  // extern "C"

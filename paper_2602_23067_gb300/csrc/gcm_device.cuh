@@ -1,0 +1,186 @@
+// gcm_device.cuh -- device-side building blocks of the AES-GCM hot path.
+//
+// Representations used on the device:
+//   * "memory words": a 16-byte block loaded as four little-endian uint32
+//     (word i = bytes 4i..4i+3).  Data, keystream and the GHASH table entries
+//     stay in this layout so that XOR-accumulation needs no byte swapping.
+//   * "poly words" (gf128): the same block with every word byte-swapped, so
+//     that the coefficient of x^i (GCM's bit-reflected convention, SP 800-38D
+//     sec. 6.3: bit 0 of the block is the MSB of byte 0 and is x^0) sits at
+//     bit 31 - (i mod 32) of word i/32.  Multiplication by x is then a
+//     right shift of the 128-bit value, with x^128 = x^7 + x^2 + x + 1
+//     folding back as R = 0xE1000000 into word 0.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gcmgpu {
+
+struct gf128 {
+    uint32_t w[4];
+};
+
+__host__ __device__ __forceinline__ uint32_t bswap32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __byte_perm(x, 0, 0x0123);
+#else
+    return (x >> 24) | ((x >> 8) & 0xFF00u) | ((x << 8) & 0xFF0000u) | (x << 24);
+#endif
+}
+
+__device__ __forceinline__ gf128 gf_zero()
+{
+    gf128 r;
+    r.w[0] = r.w[1] = r.w[2] = r.w[3] = 0u;
+    return r;
+}
+
+__device__ __forceinline__ gf128 gf_xor(const gf128 &a, const gf128 &b)
+{
+    gf128 r;
+#pragma unroll
+    for (int i = 0; i < 4; i++) r.w[i] = a.w[i] ^ b.w[i];
+    return r;
+}
+
+// memory words <-> poly words
+__device__ __forceinline__ gf128 gf_from_mem(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3)
+{
+    gf128 r;
+    r.w[0] = bswap32(m0);
+    r.w[1] = bswap32(m1);
+    r.w[2] = bswap32(m2);
+    r.w[3] = bswap32(m3);
+    return r;
+}
+
+__device__ __forceinline__ uint4 gf_to_mem(const gf128 &a)
+{
+    return make_uint4(bswap32(a.w[0]), bswap32(a.w[1]), bswap32(a.w[2]), bswap32(a.w[3]));
+}
+
+// a * x (one step of the V chain of the shift-and-add multiplier).
+__device__ __forceinline__ gf128 gf_mul_x(const gf128 &v)
+{
+    gf128 r;
+    uint32_t carry = 0u - (v.w[3] & 1u);
+    r.w[3] = __funnelshift_r(v.w[3], v.w[2], 1);
+    r.w[2] = __funnelshift_r(v.w[2], v.w[1], 1);
+    r.w[1] = __funnelshift_r(v.w[1], v.w[0], 1);
+    r.w[0] = (v.w[0] >> 1) ^ (carry & 0xE1000000u);
+    return r;
+}
+
+// General product a * b: shift-and-add over the 128 coefficients of a,
+// lowest power first.  Used for the rare multiplications (key setup, the
+// per-thread and per-tile combine); the per-block multiplications of the hot
+// loop go through the shared-memory table instead.
+static __device__ __noinline__ gf128 gf_mul(gf128 a, gf128 b)
+{
+    gf128 z = gf_zero();
+    gf128 v = b;
+#pragma unroll 1
+    for (int wi = 0; wi < 4; wi++) {
+        uint32_t aw = a.w[wi];
+#pragma unroll 8
+        for (int bit = 0; bit < 32; bit++) {
+            uint32_t m = (uint32_t)((int32_t)(aw << bit) >> 31);
+#pragma unroll
+            for (int k = 0; k < 4; k++) z.w[k] ^= v.w[k] & m;
+            v = gf_mul_x(v);
+        }
+    }
+    return z;
+}
+
+// Spreads the 16 bits of x so that bit q lands on bit 2q (zeros between).
+__device__ __forceinline__ uint32_t spread16(uint32_t x)
+{
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// a^2.  Squaring is linear over GF(2): (sum a_i x^i)^2 = sum a_i x^(2i).
+// The 128 coefficients are spread into a 256-coefficient product, whose
+// upper half is folded back with x^128 = 1 + x + x^2 + x^7.
+__device__ __forceinline__ gf128 gf_sqr(const gf128 &a)
+{
+    // In poly words, coefficient 32*wi + j sits at bit 31 - j of word wi and
+    // goes to coefficient 64*wi + 2j: the upper 16 bits of word wi fill word
+    // 2wi of the product and the lower 16 bits fill word 2wi + 1, each bit p
+    // moving to bit 2(p mod 16) + 1.
+    uint32_t p[8];
+#pragma unroll
+    for (int wi = 0; wi < 4; wi++) {
+        p[2 * wi] = spread16(a.w[wi] >> 16) << 1;
+        p[2 * wi + 1] = spread16(a.w[wi]) << 1;
+    }
+    // High half h (coefficients 128..255 as a 128-bit poly value) times
+    // (1 + x + x^2 + x^7) added into the low half.
+    const uint32_t h0 = p[4], h1 = p[5], h2 = p[6], h3 = p[7];
+    gf128 r;
+    r.w[3] = p[3] ^ h3 ^ __funnelshift_r(h3, h2, 1) ^ __funnelshift_r(h3, h2, 2) ^ __funnelshift_r(h3, h2, 7);
+    r.w[2] = p[2] ^ h2 ^ __funnelshift_r(h2, h1, 1) ^ __funnelshift_r(h2, h1, 2) ^ __funnelshift_r(h2, h1, 7);
+    r.w[1] = p[1] ^ h1 ^ __funnelshift_r(h1, h0, 1) ^ __funnelshift_r(h1, h0, 2) ^ __funnelshift_r(h1, h0, 7);
+    r.w[0] = p[0] ^ h0 ^ (h0 >> 1) ^ (h0 >> 2) ^ (h0 >> 7);
+    // Coefficients pushed past x^127 by the shifts (the low 7 bits of h3)
+    // come back once more: coefficient 128 + e folds to x^e (1+x+x^2+x^7).
+    uint32_t ov = ((h3 & 1u) << 31) ^ ((h3 & 3u) << 30) ^ ((h3 & 0x7Fu) << 25);
+    r.w[0] ^= ov ^ (ov >> 1) ^ (ov >> 2) ^ (ov >> 7);
+    return r;
+}
+
+// ---------------------------------------------------------------------
+// AES: S-box from GF(2^8) (FIPS-197 sec. 5.1.1), built with log/antilog
+// tables over the generator 0x03 and the affine map written as rotations.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint8_t gf8_xtime(uint8_t a)
+{
+    return (uint8_t)((a << 1) ^ ((a & 0x80) ? 0x1B : 0x00));
+}
+
+__device__ __forceinline__ uint8_t rotl8(uint8_t x, int s)
+{
+    return (uint8_t)((x << s) | (x >> (8 - s)));
+}
+
+// Fills sbox[256] (call with one block of >= 256 threads; uses smem scratch
+// of 512 bytes passed in).
+__device__ inline void build_sbox_block(uint8_t *sbox, uint8_t *scratch_exp, uint8_t *scratch_log)
+{
+    if (threadIdx.x == 0) {
+        uint8_t x = 1;
+        for (int i = 0; i < 255; i++) {
+            scratch_exp[i] = x;
+            scratch_log[x] = (uint8_t)i;
+            x = (uint8_t)(x ^ gf8_xtime(x)); // x * 0x03
+        }
+        scratch_exp[255] = 1;
+        scratch_log[0] = 0;
+    }
+    __syncthreads();
+    int t = threadIdx.x;
+    if (t < 256) {
+        uint8_t inv = (t == 0) ? 0 : scratch_exp[(255 - scratch_log[t]) % 255];
+        uint8_t s = (uint8_t)(inv ^ rotl8(inv, 1) ^ rotl8(inv, 2) ^ rotl8(inv, 3) ^ rotl8(inv, 4) ^ 0x63);
+        sbox[t] = s;
+    }
+    __syncthreads();
+}
+
+// Round-table entry for table r (0..3) and S-box output s, as a little-endian
+// word whose byte i is row i of the MixColumns column: T_r[v] is column r of
+// the matrix [2 3 1 1; 1 2 3 1; 1 1 2 3; 3 1 1 2] times S[v].
+__device__ __forceinline__ uint32_t ttable_entry(int r, uint8_t s)
+{
+    uint32_t s1 = s, s2 = gf8_xtime(s), s3 = s2 ^ s1;
+    uint32_t t0 = s2 | (s1 << 8) | (s1 << 16) | (s3 << 24);
+    return (t0 << (8 * r)) | (r ? (t0 >> (32 - 8 * r)) : 0u);
+}
+
+} // namespace gcmgpu

@@ -1,0 +1,108 @@
+// gcm_internal.h -- device data layouts and kernel launchers shared by the
+// kernel file and the C-ABI implementation.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gcm_device.cuh"
+
+namespace gcmgpu {
+
+// Threads per CTA of the fused map kernel.  It is also the interleave stride
+// of the per-thread Horner chains (thread t of a tile takes blocks t, t+T,
+// t+2T, ...), so the key setup builds its table for the constant H^T.
+constexpr int KF_THREADS = 512;
+constexpr int KF_LOG2_THREADS = 9;
+constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
+constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
+
+// Shared-memory map of the fused kernel (byte offsets into dynamic smem).
+constexpr uint32_t SM_T01 = 0;         // rows v: [T0[v] x 32 lanes | T1[v] x 32 lanes]
+constexpr uint32_t SM_T23 = 65536;     // rows v: [T2[v] x 32 lanes | T3[v] x 32 lanes]
+constexpr uint32_t SM_GTAB = 131072;   // rows v: 16 positions x 16 bytes
+constexpr uint32_t SM_RED = 196608;    // cross-warp reduction slots
+constexpr uint32_t KF_SMEM_BYTES = SM_RED + (KF_THREADS / 32) * 16;
+
+// Per-key material, built on the device by the key-setup kernel.
+struct KeyMat {
+    uint32_t rk[60];            // round keys, memory words (FIPS-197 sec. 5.2)
+    uint32_t nr;                // 10, 12 or 14
+    uint32_t pad_[3];
+    gf128 H;                    // hash subkey E_K(0^128), poly words
+    gf128 h2k[H2K_COUNT];       // H^(2^k): the stride table of the tree (Sec. 3.3.1)
+    gf128 hpow[KF_THREADS];     // H^1 .. H^T: per-thread closing factors
+    uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^T, memory words
+};
+
+// Per-message material.
+struct MsgMat {
+    uint32_t j0[4];   // pre-counter block J0, memory words
+    uint32_t ej0[4];  // E_K(J0), memory words
+};
+
+// Device-resident constants built once per context.
+struct DevTables {
+    uint8_t sbox[256];
+    uint32_t ttab[4 * 256];  // T0..T3
+};
+
+constexpr int IV_INLINE_MAX = 256;
+
+struct KsParams {
+    uint8_t key[32];
+    uint32_t key_len;
+    uint32_t iv_len;
+    uint8_t iv_inline[IV_INLINE_MAX];
+    const uint8_t *iv_dev;      // used when iv_len > IV_INLINE_MAX
+    KeyMat *km;
+    MsgMat *mm;
+    const DevTables *tabs;
+};
+
+struct KfParams {
+    const uint8_t *in;      // payload read (pt for encrypt, ct for decrypt)
+    uint8_t *out;           // payload written
+    const uint8_t *aad;
+    uint64_t len;           // payload bytes
+    uint64_t aad_len;
+    uint64_t a_blocks;      // ceil(aad_len / 16)
+    uint64_t n_full;        // len / 16 (whole payload blocks)
+    uint64_t M;             // a_blocks + ceil(len / 16): GHASH blocks before the length block
+    uint64_t K;             // number of tiles
+    uint32_t tile_log2;     // tile = 2^tile_log2 blocks, aligned to the end of the sequence
+    uint32_t decrypt;
+    const KeyMat *km;
+    const MsgMat *mm;
+    const DevTables *tabs;
+    gf128 *partials;        // K tile partials, poly words
+};
+
+struct KcParams {
+    gf128 *partials;        // K partials (overwritten: used as the tree's scratch)
+    gf128 *scratch;         // K/2 + 1 entries
+    uint64_t K;
+    uint32_t tile_log2;
+    uint64_t aad_len;
+    uint64_t len;
+    const KeyMat *km;
+    const MsgMat *mm;
+    uint8_t *tag_out;       // 16 bytes (device), may be null
+    const uint8_t *tag_expected;  // 16 bytes (device) for decrypt, else null
+    int32_t *status;        // device status word (decrypt), may be null
+};
+
+struct KzParams {
+    uint8_t *out;
+    uint64_t len;
+    const int32_t *status;
+};
+
+// Launchers (defined in gcm_kernels.cu).  All are asynchronous on `stream`.
+cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream);
+cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream);
+cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
+cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);
+cudaError_t configure_kernels();  // sets the dynamic shared memory limit
+
+}  // namespace gcmgpu

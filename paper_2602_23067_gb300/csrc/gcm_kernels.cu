@@ -1,0 +1,585 @@
+// gcm_kernels.cu -- the AES-GCM hot path on sm_103a.
+//
+// Kernels (one pass over the payload; the paper's CTR kernel and GHASH map
+// kernel, Sec. 3.3.2 and 5.2.3, are fused into KF):
+//   build_tables  once per context: S-box from GF(2^8) and the four AES
+//                 round tables T0..T3 (FIPS-197 sec. 5.1).
+//   KS  key_setup per key/message: key expansion (FIPS-197 sec. 5.2),
+//                 H = E_K(0^128), J0 (SP 800-38D Alg. 4 step 2), E_K(J0),
+//                 the stride table H^(2^k) (Sec. 3.3.1), H^1..H^T and the
+//                 8-bit multiplication table of H^T.
+//   KF  fused     AES-CTR keystream + XOR (geometry-agnostic counters,
+//                 Sec. 5.2: block j always uses inc32^(j+1)(J0)) fused with
+//                 the GHASH map: every CTA reduces tiles of the GHASH input
+//                 sequence A||C to 16-byte partials (Sec. 5.2.3, map phase).
+//   KC  combine   log-depth tree over the tile partials with multipliers
+//                 H^(2^k) (Sec. 3.3.1, Fig. 2b; Sec. 5.2.3 reduce phase),
+//                 the length block and T = E_K(J0) xor GHASH; for decryption
+//                 the constant-time tag check (Sec. 3.3.2 item 4).
+//   KZ  zero_fill on an authentication failure the output payload is zeroed
+//                 (payload suppression, Sec. 4.2).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gcm_internal.h"
+
+namespace gcmgpu {
+
+// ---------------------------------------------------------------------
+// Tables, once per context
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256) build_tables_kernel(DevTables *tabs)
+{
+    __shared__ uint8_t sbox[256], ex[256], lg[256];
+    build_sbox_block(sbox, ex, lg);
+    const int t = threadIdx.x;
+    tabs->sbox[t] = sbox[t];
+#pragma unroll
+    for (int r = 0; r < 4; r++) tabs->ttab[r * 256 + t] = ttable_entry(r, sbox[t]);
+}
+
+// ---------------------------------------------------------------------
+// Single-block AES used by the key setup (H and E_K(J0) only).
+// State: four memory words, word c = column c, byte r = row r.
+// ---------------------------------------------------------------------
+__device__ void aes_block_bytes(const uint32_t *rkw, int nr, const uint8_t *sbox,
+                                const uint32_t in[4], uint32_t out[4])
+{
+    uint32_t s[4];
+    for (int c = 0; c < 4; c++) s[c] = in[c] ^ rkw[c];
+    for (int round = 1; round <= nr; round++) {
+        uint32_t t[4];
+        for (int c = 0; c < 4; c++) {
+            // SubBytes + ShiftRows: row r of column c comes from column c + r.
+            uint32_t b0 = sbox[(s[c] >> 0) & 0xFF];
+            uint32_t b1 = sbox[(s[(c + 1) & 3] >> 8) & 0xFF];
+            uint32_t b2 = sbox[(s[(c + 2) & 3] >> 16) & 0xFF];
+            uint32_t b3 = sbox[(s[(c + 3) & 3] >> 24) & 0xFF];
+            if (round < nr) {
+                // MixColumns: row r = 2a_r ^ 3a_{r+1} ^ a_{r+2} ^ a_{r+3}.
+                uint8_t a[4] = {(uint8_t)b0, (uint8_t)b1, (uint8_t)b2, (uint8_t)b3};
+                uint8_t m[4];
+                for (int r = 0; r < 4; r++) {
+                    uint8_t x = a[r], y = a[(r + 1) & 3];
+                    m[r] = (uint8_t)(gf8_xtime(x) ^ gf8_xtime(y) ^ y ^ a[(r + 2) & 3] ^ a[(r + 3) & 3]);
+                }
+                t[c] = (uint32_t)m[0] | ((uint32_t)m[1] << 8) | ((uint32_t)m[2] << 16) | ((uint32_t)m[3] << 24);
+            } else {
+                t[c] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
+            }
+        }
+        for (int c = 0; c < 4; c++) s[c] = t[c] ^ rkw[4 * round + c];
+    }
+    for (int c = 0; c < 4; c++) out[c] = s[c];
+}
+
+// Key expansion (FIPS-197 sec. 5.2) into memory words.  Word i holds bytes
+// 4i..4i+3 of the schedule with the first byte in the low bits, so RotWord is
+// a right rotation by 8 and Rcon enters the low byte.
+__device__ int key_expand_words(const uint8_t *key, int key_len, const uint8_t *sbox, uint32_t *w)
+{
+    const int nk = key_len / 4;
+    const int nr = nk + 6;
+    for (int i = 0; i < nk; i++)
+        w[i] = (uint32_t)key[4 * i] | ((uint32_t)key[4 * i + 1] << 8) |
+               ((uint32_t)key[4 * i + 2] << 16) | ((uint32_t)key[4 * i + 3] << 24);
+    uint8_t rcon = 1;
+    for (int i = nk; i < 4 * (nr + 1); i++) {
+        uint32_t t = w[i - 1];
+        if (i % nk == 0) {
+            t = (t >> 8) | (t << 24);
+            t = (uint32_t)sbox[t & 0xFF] | ((uint32_t)sbox[(t >> 8) & 0xFF] << 8) |
+                ((uint32_t)sbox[(t >> 16) & 0xFF] << 16) | ((uint32_t)sbox[t >> 24] << 24);
+            t ^= rcon;
+            rcon = gf8_xtime(rcon);
+        } else if (nk > 6 && i % nk == 4) {
+            t = (uint32_t)sbox[t & 0xFF] | ((uint32_t)sbox[(t >> 8) & 0xFF] << 8) |
+                ((uint32_t)sbox[(t >> 16) & 0xFF] << 16) | ((uint32_t)sbox[t >> 24] << 24);
+        }
+        w[i] = w[i - nk] ^ t;
+    }
+    return nr;
+}
+
+// ---------------------------------------------------------------------
+// KS: per-key / per-message setup (one CTA of 256 threads)
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ KsParams p)
+{
+    __shared__ uint8_t sbox[256];
+    __shared__ uint32_t rkw[60];
+    __shared__ gf128 sH;
+    __shared__ gf128 sh2k[H2K_COUNT];
+    __shared__ gf128 basis[128];
+    __shared__ int s_nr;
+    const int t = threadIdx.x;
+    KeyMat *km = p.km;
+
+    sbox[t] = p.tabs->sbox[t];
+    __syncthreads();
+    if (t == 0) {
+        int nr = key_expand_words(p.key, (int)p.key_len, sbox, rkw);
+        s_nr = nr;
+        uint32_t zero[4] = {0u, 0u, 0u, 0u}, h[4];
+        aes_block_bytes(rkw, nr, sbox, zero, h);
+        sH = gf_from_mem(h[0], h[1], h[2], h[3]);
+    }
+    __syncthreads();
+    const int nr = s_nr;
+    if (t == 0) {
+        // Stride table H^(2^k) by repeated squaring.
+        gf128 cur = sH;
+        for (int k = 0; k < H2K_COUNT; k++) {
+            sh2k[k] = cur;
+            km->h2k[k] = cur;
+            cur = gf_sqr(cur);
+        }
+        km->H = sH;
+        km->nr = (uint32_t)nr;
+    } else if (t == 32) {
+        // J0: IV || 0^31 || 1 for a 96-bit IV, else GHASH_H(IV || pad || [len(IV)]_64).
+        const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
+        uint32_t j0[4];
+        if (p.iv_len == 12) {
+            for (int i = 0; i < 3; i++)
+                j0[i] = (uint32_t)iv[4 * i] | ((uint32_t)iv[4 * i + 1] << 8) |
+                        ((uint32_t)iv[4 * i + 2] << 16) | ((uint32_t)iv[4 * i + 3] << 24);
+            j0[3] = 0x01000000u;  // bytes 12..15 = 00 00 00 01
+        } else {
+            gf128 y = gf_zero();
+            for (uint32_t off = 0; off < p.iv_len; off += 16) {
+                uint32_t m[4] = {0u, 0u, 0u, 0u};
+                for (uint32_t b = 0; b < 16 && off + b < p.iv_len; b++)
+                    m[b >> 2] |= (uint32_t)iv[off + b] << (8 * (b & 3));
+                y = gf_mul(gf_xor(y, gf_from_mem(m[0], m[1], m[2], m[3])), sH);
+            }
+            gf128 lb = gf_zero();
+            const uint64_t bits = (uint64_t)p.iv_len * 8u;
+            lb.w[2] = (uint32_t)(bits >> 32);
+            lb.w[3] = (uint32_t)bits;
+            y = gf_mul(gf_xor(y, lb), sH);
+            uint4 jm = gf_to_mem(y);
+            j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
+        }
+        uint32_t e[4];
+        aes_block_bytes(rkw, nr, sbox, j0, e);
+        for (int i = 0; i < 4; i++) {
+            p.mm->j0[i] = j0[i];
+            p.mm->ej0[i] = e[i];
+        }
+    } else if (t >= 64 && t < 64 + 60) {
+        km->rk[t - 64] = (t - 64 < 4 * (nr + 1)) ? rkw[t - 64] : 0u;
+    }
+    __syncthreads();
+    if (t == 0) {
+        // basis[i] = x^i * H^T: the 128 single-coefficient products.
+        gf128 v = sh2k[KF_LOG2_THREADS];
+        for (int i = 0; i < 128; i++) {
+            basis[i] = v;
+            v = gf_mul_x(v);
+        }
+    }
+    // H^e for e = 1..T as a product of stride-table entries.
+    for (int e = t + 1; e <= KF_THREADS; e += blockDim.x) {
+        gf128 acc;
+        bool have = false;
+        for (int k = 0; k <= KF_LOG2_THREADS; k++) {
+            if ((e >> k) & 1) {
+                acc = have ? gf_mul(acc, sh2k[k]) : sh2k[k];
+                have = true;
+            }
+        }
+        km->hpow[e - 1] = acc;
+    }
+    __syncthreads();
+    // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^T.
+    // Bit b of v (LSB = 0) is the coefficient of x^(8k + 7 - b).
+    for (int idx = t; idx < GTAB_ENTRIES; idx += blockDim.x) {
+        const int v = idx >> 4, k = idx & 15;
+        gf128 acc = gf_zero();
+        for (int b = 0; b < 8; b++)
+            if ((v >> b) & 1) acc = gf_xor(acc, basis[8 * k + 7 - b]);
+        km->gtab[idx] = gf_to_mem(acc);
+    }
+}
+
+// ---------------------------------------------------------------------
+// KF: fused CTR + GHASH map
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lds32(const uint8_t *base, uint32_t off)
+{
+    return *reinterpret_cast<const uint32_t *>(base + off);
+}
+
+__device__ __forceinline__ uint4 lds128(const uint8_t *base, uint32_t off)
+{
+    return *reinterpret_cast<const uint4 *>(base + off);
+}
+
+__device__ __forceinline__ void xor4(uint4 &a, const uint4 &b)
+{
+    a.x ^= b.x; a.y ^= b.y; a.z ^= b.z; a.w ^= b.w;
+}
+
+// Address of a round-table entry: byte `BYTE` of w selects the row (bits
+// 8..15 of the address) and c holds this lane's column inside the row
+// (lane * 4, plus 128 for the odd table of the pair).  Every lane reads its
+// own bank, so a warp-wide lookup never conflicts.
+#define TADDR(w, BYTE, c) __byte_perm((w), (c), 0x5504u | ((BYTE) << 4))
+
+struct LaneConst {
+    uint32_t cA, cB;        // round-table lane offsets
+    uint32_t selA, selB;    // byte rotations for the GHASH lookups
+    uint32_t cg[8];         // GHASH table slot offsets per lookup step
+};
+
+__device__ __forceinline__ LaneConst make_lane_const(int lane)
+{
+    LaneConst L;
+    L.cA = (uint32_t)lane * 4u;
+    L.cB = 128u + (uint32_t)lane * 4u;
+    const uint32_t r8 = (uint32_t)lane & 7u;
+    L.selA = 0u;
+    L.selB = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        L.selA |= ((r8 + j) & 7u) << (4 * j);
+        L.selB |= ((r8 + 4 + j) & 7u) << (4 * j);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; i++) L.cg[i] = ((i + r8) & 7u) << 4;
+    return L;
+}
+
+// a * H^T through the shared 8-bit table: the XOR of 16 entries, one per
+// byte position.  Lanes of a quarter-warp visit the positions of each half
+// in rotated order, so their 16-byte reads fall in 8 distinct bank groups.
+__device__ __forceinline__ uint4 ghash_mul_table(const uint8_t *smem, const uint4 &a, const LaneConst &L)
+{
+    const uint8_t *g = smem + SM_GTAB;
+    const uint32_t y0 = __byte_perm(a.x, a.y, L.selA);
+    const uint32_t y1 = __byte_perm(a.x, a.y, L.selB);
+    const uint32_t y2 = __byte_perm(a.z, a.w, L.selA);
+    const uint32_t y3 = __byte_perm(a.z, a.w, L.selB);
+    uint4 r = lds128(g, TADDR(y0, 0, L.cg[0]));
+    xor4(r, lds128(g, TADDR(y0, 1, L.cg[1])));
+    xor4(r, lds128(g, TADDR(y0, 2, L.cg[2])));
+    xor4(r, lds128(g, TADDR(y0, 3, L.cg[3])));
+    xor4(r, lds128(g, TADDR(y1, 0, L.cg[4])));
+    xor4(r, lds128(g, TADDR(y1, 1, L.cg[5])));
+    xor4(r, lds128(g, TADDR(y1, 2, L.cg[6])));
+    xor4(r, lds128(g, TADDR(y1, 3, L.cg[7])));
+    const uint8_t *g2 = g + 128;
+    xor4(r, lds128(g2, TADDR(y2, 0, L.cg[0])));
+    xor4(r, lds128(g2, TADDR(y2, 1, L.cg[1])));
+    xor4(r, lds128(g2, TADDR(y2, 2, L.cg[2])));
+    xor4(r, lds128(g2, TADDR(y2, 3, L.cg[3])));
+    xor4(r, lds128(g2, TADDR(y3, 0, L.cg[4])));
+    xor4(r, lds128(g2, TADDR(y3, 1, L.cg[5])));
+    xor4(r, lds128(g2, TADDR(y3, 2, L.cg[6])));
+    xor4(r, lds128(g2, TADDR(y3, 3, L.cg[7])));
+    return r;
+}
+
+// One AES encryption of a counter block through the replicated round tables.
+// s0..s2 already hold (J0 word xor round key 0); w3 is the counter word.
+template <int NR>
+__device__ __forceinline__ uint4 aes_ctr_block(const uint8_t *smem, const uint32_t *rk,
+                                               uint32_t s0, uint32_t s1, uint32_t s2, uint32_t w3,
+                                               const LaneConst &L)
+{
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    uint32_t s3 = w3 ^ rk[3];
+#pragma unroll
+    for (int r = 1; r < NR; r++) {
+        const uint32_t n0 = lds32(t01, TADDR(s0, 0, L.cA)) ^ lds32(t01, TADDR(s1, 1, L.cB)) ^
+                            lds32(t23, TADDR(s2, 2, L.cA)) ^ lds32(t23, TADDR(s3, 3, L.cB)) ^ rk[4 * r + 0];
+        const uint32_t n1 = lds32(t01, TADDR(s1, 0, L.cA)) ^ lds32(t01, TADDR(s2, 1, L.cB)) ^
+                            lds32(t23, TADDR(s3, 2, L.cA)) ^ lds32(t23, TADDR(s0, 3, L.cB)) ^ rk[4 * r + 1];
+        const uint32_t n2 = lds32(t01, TADDR(s2, 0, L.cA)) ^ lds32(t01, TADDR(s3, 1, L.cB)) ^
+                            lds32(t23, TADDR(s0, 2, L.cA)) ^ lds32(t23, TADDR(s1, 3, L.cB)) ^ rk[4 * r + 2];
+        const uint32_t n3 = lds32(t01, TADDR(s3, 0, L.cA)) ^ lds32(t01, TADDR(s0, 1, L.cB)) ^
+                            lds32(t23, TADDR(s1, 2, L.cA)) ^ lds32(t23, TADDR(s2, 3, L.cB)) ^ rk[4 * r + 3];
+        s0 = n0; s1 = n1; s2 = n2; s3 = n3;
+    }
+    // Final round: SubBytes + ShiftRows + AddRoundKey.  S[v] is byte 0 of
+    // T2[v], byte 1 of T3[v], byte 2 of T0[v] and byte 3 of T1[v].
+    uint4 o;
+#define LAST_COL(OUT, a, b, c, d, RK)                                                  \
+    {                                                                                   \
+        const uint32_t e0 = lds32(t23, TADDR(a, 0, L.cA));                              \
+        const uint32_t e1 = lds32(t23, TADDR(b, 1, L.cB));                              \
+        const uint32_t e2 = lds32(t01, TADDR(c, 2, L.cA));                              \
+        const uint32_t e3 = lds32(t01, TADDR(d, 3, L.cB));                              \
+        OUT = __byte_perm(__byte_perm(e0, e1, 0x3250u), __byte_perm(e2, e3, 0x7210u), 0x7610u) ^ (RK); \
+    }
+    LAST_COL(o.x, s0, s1, s2, s3, rk[4 * NR + 0]);
+    LAST_COL(o.y, s1, s2, s3, s0, rk[4 * NR + 1]);
+    LAST_COL(o.z, s2, s3, s0, s1, rk[4 * NR + 2]);
+    LAST_COL(o.w, s3, s0, s1, s2, rk[4 * NR + 3]);
+#undef LAST_COL
+    return o;
+}
+
+__device__ __forceinline__ uint4 load_partial(const uint8_t *src, uint32_t nbytes)
+{
+    uint32_t m[4] = {0u, 0u, 0u, 0u};
+    for (uint32_t b = 0; b < nbytes; b++) m[b >> 2] |= (uint32_t)src[b] << (8 * (b & 3));
+    return make_uint4(m[0], m[1], m[2], m[3]);
+}
+
+__device__ __forceinline__ void store_partial(uint8_t *dst, const uint4 &v, uint32_t nbytes)
+{
+    const uint32_t m[4] = {v.x, v.y, v.z, v.w};
+    for (uint32_t b = 0; b < nbytes; b++) dst[b] = (uint8_t)(m[b >> 2] >> (8 * (b & 3)));
+}
+
+template <int NR>
+__global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31;
+    const int warp = tid >> 5;
+
+    // Stage the replicated round tables and this key's GHASH table.
+    {
+        const uint32_t *tt = p.tabs->ttab;
+        uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
+        for (int w = tid; w < 32768; w += KF_THREADS) {
+            const int region = w >> 14, v = (w >> 6) & 255, odd = (w >> 5) & 1;
+            s32[w] = __ldg(&tt[(2 * region + odd) * 256 + v]);
+        }
+        const uint4 *g = p.km->gtab;
+        uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
+        for (int i = tid; i < GTAB_ENTRIES; i += KF_THREADS) sg[i] = __ldg(&g[i]);
+    }
+    uint32_t rk[4 * (NR + 1)];
+#pragma unroll
+    for (int i = 0; i < 4 * (NR + 1); i++) rk[i] = __ldg(&p.km->rk[i]);
+    const uint32_t s0 = __ldg(&p.mm->j0[0]) ^ rk[0];
+    const uint32_t s1 = __ldg(&p.mm->j0[1]) ^ rk[1];
+    const uint32_t s2 = __ldg(&p.mm->j0[2]) ^ rk[2];
+    const uint32_t ctr0 = bswap32(__ldg(&p.mm->j0[3]));
+    const LaneConst L = make_lane_const(lane);
+    gf128 *red = reinterpret_cast<gf128 *>(smem + SM_RED);
+    const uint64_t a_blocks = p.a_blocks;
+    const uint64_t n_full = p.n_full;
+    const bool dec = p.decrypt != 0;
+    __syncthreads();
+
+    for (uint64_t tile = blockIdx.x; tile < p.K; tile += gridDim.x) {
+        const uint64_t tile_blocks = 1ull << p.tile_log2;
+        const uint64_t tend = p.M - ((p.K - 1 - tile) << p.tile_log2);
+        const uint64_t tbeg = (tend > tile_blocks) ? tend - tile_blocks : 0ull;
+        const uint32_t tlen = (uint32_t)(tend - tbeg);
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+
+        if (tbeg >= a_blocks && tend <= a_blocks + n_full) {
+            // Whole payload blocks only.
+            const uint64_t j_base = tbeg - a_blocks;
+            const uint4 *in = reinterpret_cast<const uint4 *>(p.in) + j_base;
+            uint4 *out = reinterpret_cast<uint4 *>(p.out) + j_base;
+            for (uint32_t sl = tid; sl < tlen; sl += KF_THREADS) {
+                const uint4 din = __ldcs(in + sl);
+                const uint32_t ctr = ctr0 + 1u + (uint32_t)(j_base + sl);
+                uint4 ks = aes_ctr_block<NR>(smem, rk, s0, s1, s2, bswap32(ctr), L);
+                ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                __stcs(out + sl, ks);
+                uint4 m = ghash_mul_table(smem, acc, L);
+                xor4(m, dec ? din : ks);
+                acc = m;
+            }
+        } else {
+            // Tiles that touch the AAD or the final partial block.
+            for (uint32_t sl = tid; sl < tlen; sl += KF_THREADS) {
+                const uint64_t s = tbeg + sl;
+                uint4 x;
+                if (s < a_blocks) {
+                    const uint64_t off = s * 16u;
+                    const uint64_t rem = p.aad_len - off;
+                    const uint8_t *src = p.aad + off;
+                    if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
+                        x = *reinterpret_cast<const uint4 *>(src);
+                    else
+                        x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
+                } else {
+                    const uint64_t j = s - a_blocks;
+                    const uint32_t ctr = ctr0 + 1u + (uint32_t)j;
+                    uint4 ks = aes_ctr_block<NR>(smem, rk, s0, s1, s2, bswap32(ctr), L);
+                    if (j < n_full) {
+                        const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(p.in) + j);
+                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                        __stcs(reinterpret_cast<uint4 *>(p.out) + j, ks);
+                        x = dec ? din : ks;
+                    } else {
+                        const uint32_t nb = (uint32_t)(p.len - j * 16u);
+                        const uint4 din = load_partial(p.in + j * 16u, nb);
+                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                        // keep only the nb valid bytes of the ciphertext block
+                        uint4 c = load_partial(reinterpret_cast<const uint8_t *>(&ks), nb);
+                        store_partial(p.out + j * 16u, c, nb);
+                        x = dec ? din : c;
+                    }
+                }
+                uint4 m = ghash_mul_table(smem, acc, L);
+                xor4(m, x);
+                acc = m;
+            }
+        }
+
+        // Close this thread's chain: its last block sits e blocks before the
+        // tile end, so the chain value is multiplied by H^e (1 <= e <= T).
+        gf128 z = gf_zero();
+        if ((uint32_t)tid < tlen) {
+            const uint32_t q = (tlen - tid + KF_THREADS - 1) / KF_THREADS;
+            const uint32_t e = tlen - tid - KF_THREADS * (q - 1);
+            z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), p.km->hpow[e - 1]);
+        }
+        // XOR-reduce the CTA's contributions into the tile partial.
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
+        if (lane == 0) red[warp] = z;
+        __syncthreads();
+        if (warp == 0) {
+            z = (lane < KF_THREADS / 32) ? red[lane] : gf_zero();
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
+            if (lane == 0) p.partials[tile] = z;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------
+// KC: log-depth combine + tag (one CTA)
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ KcParams p)
+{
+    const int t = threadIdx.x;
+    const KeyMat *km = p.km;
+    uint64_t cnt = p.K;
+    int level = 0;
+    // Level 0 reads the partials right to left (index g counts tiles from
+    // the end of the sequence), so every right-hand operand is a full group
+    // of 2^level tiles and its multiplier is exactly H^(2^(tile_log2+level)).
+    gf128 *src = p.partials;
+    gf128 *dst = p.scratch;
+    bool reversed = true;
+    while (cnt > 1) {
+        const uint64_t half = (cnt + 1) / 2;
+        const gf128 mult = km->h2k[p.tile_log2 + level];
+        for (uint64_t g = t; g < half; g += blockDim.x) {
+            const uint64_t ri = 2 * g, li = 2 * g + 1;
+            const gf128 right = reversed ? src[cnt - 1 - ri] : src[ri];
+            gf128 v = right;
+            if (li < cnt) {
+                const gf128 left = reversed ? src[cnt - 1 - li] : src[li];
+                v = gf_xor(gf_mul(left, mult), right);
+            }
+            dst[g] = v;
+        }
+        __syncthreads();
+        gf128 *tmp = src;
+        src = dst;
+        dst = tmp;
+        reversed = false;
+        cnt = half;
+        level++;
+    }
+    if (t == 0) {
+        gf128 s = (cnt == 1) ? src[0] : gf_zero();
+        // Length block [len(A)]_64 || [len(C)]_64 in bits (SP 800-38D Alg. 4 step 5).
+        gf128 lb;
+        const uint64_t abits = p.aad_len * 8u, cbits = p.len * 8u;
+        lb.w[0] = (uint32_t)(abits >> 32);
+        lb.w[1] = (uint32_t)abits;
+        lb.w[2] = (uint32_t)(cbits >> 32);
+        lb.w[3] = (uint32_t)cbits;
+        const gf128 gh = gf_mul(gf_xor(s, lb), km->H);
+        const uint4 gm = gf_to_mem(gh);
+        const uint32_t tw[4] = {gm.x ^ p.mm->ej0[0], gm.y ^ p.mm->ej0[1], gm.z ^ p.mm->ej0[2],
+                                gm.w ^ p.mm->ej0[3]};
+        uint8_t tag[16];
+        for (int b = 0; b < 16; b++) tag[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
+        if (p.tag_out)
+            for (int b = 0; b < 16; b++) p.tag_out[b] = tag[b];
+        if (p.tag_expected) {
+            uint32_t diff = 0;
+            for (int b = 0; b < 16; b++) diff |= (uint32_t)(tag[b] ^ p.tag_expected[b]);
+            if (p.status) *p.status = diff ? -3 : 0;
+        } else if (p.status) {
+            *p.status = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// KZ: zero-fill the payload when the tag check failed
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(256) zero_on_fail_kernel(const __grid_constant__ KzParams p)
+{
+    if (*p.status == 0) return;
+    const uint64_t nvec = p.len / 16;
+    uint4 *o = reinterpret_cast<uint4 *>(p.out);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec; i += stride)
+        o[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (blockIdx.x == 0 && threadIdx.x < (p.len & 15)) p.out[nvec * 16 + threadIdx.x] = 0;
+}
+
+// ---------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------
+cudaError_t configure_kernels()
+{
+    cudaError_t e;
+    e = cudaFuncSetAttribute(fused_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fused_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(fused_kernel<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+}
+
+cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream)
+{
+    build_tables_kernel<<<1, 256, 0, stream>>>(tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream)
+{
+    key_setup_kernel<<<1, 256, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream)
+{
+    if (p.K == 0) return cudaSuccess;
+    switch (nr) {
+    case 10: fused_kernel<10><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
+    case 12: fused_kernel<12><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
+    case 14: fused_kernel<14><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const KcParams &p, cudaStream_t stream)
+{
+    combine_kernel<<<1, 1024, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream)
+{
+    zero_on_fail_kernel<<<grid, 256, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace gcmgpu
