@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-N1 = N2 = 32768
+N1 = N2 = 32768  # default image side (the 4 GiB workload); --side changes it
 DATA_BYTES = N1 * N2 * 4
 METRIC = "AES-GCM GB/s @4GiB on 1 GB300; batched p50/p99 latency vs per-msg launch"
 WORKLOAD = "fits_4gib_aes256gcm_enc+dec"
@@ -46,13 +46,14 @@ def workload_config(n_gpus):
     from paper_2602_23067_gb300 import workloads
 
     padded = workloads.padded_len(DATA_BYTES)
+    name = WORKLOAD if N1 == 32768 else "fits_%dx%d_aes256gcm_enc+dec" % (N1, N2)
     return {
-        "workload": WORKLOAD,
+        "workload": name,
         "cipher": "AES-256-GCM",
         "iv_bits": 96,
         "aad_bytes": 2880,
         "payload_bytes": padded,
-        "image": "32768x32768 float32 BITPIX=-32, N(1000,50^2) + 10^4 Poisson point sources",
+        "image": "%dx%d float32 BITPIX=-32, N(1000,50^2) + 10^4 Poisson point sources" % (N1, N2),
         "step": "encrypt + decrypt-verify of the data unit",
         "l2": "inputs (4.3 GB) exceed L2 (129 MB); no flush",
         "per_gpu": "one 4 GiB message per GPU" if n_gpus > 1 else "one 4 GiB message",
@@ -411,7 +412,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-bytes", type=int, default=8 << 20)
+    ap.add_argument("--side", type=int, default=32768,
+                    help="image side in pixels (default 32768: the 4 GiB workload; smaller sides are for profiling)")
     args = ap.parse_args()
+    global N1, N2, DATA_BYTES
+    N1 = N2 = args.side
+    DATA_BYTES = N1 * N2 * 4
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
     if args.impl == "reference":
