@@ -8,11 +8,15 @@
 
 namespace gcmgpu {
 
-// Threads per CTA of the fused map kernel.  It is also the interleave stride
-// of the per-thread Horner chains (thread t of a tile takes blocks t, t+T,
-// t+2T, ...), so the key setup builds its table for the constant H^T.
+// Threads per CTA of the fused map kernel (16 warps).  Each warp walks one
+// contiguous segment of a tile in windows of 32 consecutive blocks, lane l
+// taking the l-th block of every window, so each lane's Horner chain has
+// stride GH_STRIDE = 32 and the key setup builds its table for H^32.
 constexpr int KF_THREADS = 512;
-constexpr int KF_LOG2_THREADS = 9;
+constexpr int KF_WARPS = KF_THREADS / 32;
+constexpr int KF_LOG2_WARPS = 4;
+constexpr int GH_STRIDE = 32;
+constexpr int GH_LOG2_STRIDE = 5;
 constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
 constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
 
@@ -20,8 +24,9 @@ constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
 constexpr uint32_t SM_T01 = 0;         // rows v: [T0[v] x 32 lanes | T1[v] x 32 lanes]
 constexpr uint32_t SM_T23 = 65536;     // rows v: [T2[v] x 32 lanes | T3[v] x 32 lanes]
 constexpr uint32_t SM_GTAB = 131072;   // rows v: 16 positions x 16 bytes
-constexpr uint32_t SM_RED = 196608;    // cross-warp reduction slots
-constexpr uint32_t KF_SMEM_BYTES = SM_RED + (KF_THREADS / 32) * 16;
+constexpr uint32_t SM_RED = 196608;    // cross-warp reduction slots (16 x 16 B)
+constexpr uint32_t SM_SEGF = SM_RED + 256;  // per-warp segment factors H^((15-w)S)
+constexpr uint32_t KF_SMEM_BYTES = SM_SEGF + KF_WARPS * 16;
 
 // Per-key material, built on the device by the key-setup kernel.
 struct KeyMat {
@@ -30,8 +35,8 @@ struct KeyMat {
     uint32_t pad_[3];
     gf128 H;                    // hash subkey E_K(0^128), poly words
     gf128 h2k[H2K_COUNT];       // H^(2^k): the stride table of the tree (Sec. 3.3.1)
-    gf128 hpow[KF_THREADS];     // H^1 .. H^T: per-thread closing factors
-    uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^T, memory words
+    gf128 hpow[GH_STRIDE];      // H^1 .. H^32: per-lane closing factors
+    uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^32, memory words
 };
 
 // Per-message material.

@@ -172,18 +172,19 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
     }
     __syncthreads();
     if (t == 0) {
-        // basis[i] = x^i * H^T: the 128 single-coefficient products.
-        gf128 v = sh2k[KF_LOG2_THREADS];
+        // basis[i] = x^i * H^32: the 128 single-coefficient products.
+        gf128 v = sh2k[GH_LOG2_STRIDE];
         for (int i = 0; i < 128; i++) {
             basis[i] = v;
             v = gf_mul_x(v);
         }
     }
-    // H^e for e = 1..T as a product of stride-table entries.
-    for (int e = t + 1; e <= KF_THREADS; e += blockDim.x) {
+    // H^e for e = 1..32 as a product of stride-table entries.
+    if (t >= 32 && t < 32 + GH_STRIDE) {
+        const int e = t - 31;
         gf128 acc;
         bool have = false;
-        for (int k = 0; k <= KF_LOG2_THREADS; k++) {
+        for (int k = 0; k <= GH_LOG2_STRIDE; k++) {
             if ((e >> k) & 1) {
                 acc = have ? gf_mul(acc, sh2k[k]) : sh2k[k];
                 have = true;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
         km->hpow[e - 1] = acc;
     }
     __syncthreads();
-    // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^T.
+    // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32.
     // Bit b of v (LSB = 0) is the coefficient of x^(8k + 7 - b).
     for (int idx = t; idx < GTAB_ENTRIES; idx += blockDim.x) {
         const int v = idx >> 4, k = idx & 15;
@@ -281,44 +282,48 @@ __device__ __forceinline__ uint4 ghash_mul_table(const uint8_t *smem, const uint
     return r;
 }
 
-// One AES encryption of a counter block through the replicated round tables.
-// s0..s2 already hold (J0 word xor round key 0); w3 is the counter word.
-template <int NR>
-__device__ __forceinline__ uint4 aes_ctr_block(const uint8_t *smem, const uint32_t *rk,
-                                               uint32_t s0, uint32_t s1, uint32_t s2, uint32_t w3,
-                                               const LaneConst &L)
+// Round-table lookups: T0/T1 live in the first 64 KiB region, T2/T3 in the
+// second; the lane's column is cA (even table) or cB (odd table).
+#define LT0(w, B) lds32(t01, TADDR((w), B, L.cA))
+#define LT1(w, B) lds32(t01, TADDR((w), B, L.cB))
+#define LT2(w, B) lds32(t23, TADDR((w), B, L.cA))
+#define LT3(w, B) lds32(t23, TADDR((w), B, L.cB))
+
+// One full AES round (SubBytes, ShiftRows, MixColumns, AddRoundKey) on the
+// state s0..s3 (memory words = columns): column c takes row r from column c+r.
+__device__ __forceinline__ void aes_round(const uint8_t *t01, const uint8_t *t23, const LaneConst &L,
+                                          uint32_t &s0, uint32_t &s1, uint32_t &s2, uint32_t &s3,
+                                          uint32_t k0, uint32_t k1, uint32_t k2, uint32_t k3)
 {
-    const uint8_t *t01 = smem + SM_T01;
-    const uint8_t *t23 = smem + SM_T23;
-    uint32_t s3 = w3 ^ rk[3];
+    const uint32_t n0 = LT0(s0, 0) ^ LT1(s1, 1) ^ LT2(s2, 2) ^ LT3(s3, 3) ^ k0;
+    const uint32_t n1 = LT0(s1, 0) ^ LT1(s2, 1) ^ LT2(s3, 2) ^ LT3(s0, 3) ^ k1;
+    const uint32_t n2 = LT0(s2, 0) ^ LT1(s3, 1) ^ LT2(s0, 2) ^ LT3(s1, 3) ^ k2;
+    const uint32_t n3 = LT0(s3, 0) ^ LT1(s0, 1) ^ LT2(s1, 2) ^ LT3(s2, 3) ^ k3;
+    s0 = n0; s1 = n1; s2 = n2; s3 = n3;
+}
+
+// Final round (no MixColumns).  S[v] is byte 0 of T2[v], byte 1 of T3[v],
+// byte 2 of T0[v] and byte 3 of T1[v].
+__device__ __forceinline__ uint32_t aes_last_col(const uint8_t *t01, const uint8_t *t23, const LaneConst &L,
+                                                 uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t k)
+{
+    const uint32_t e0 = LT2(a, 0), e1 = LT3(b, 1), e2 = LT0(c, 2), e3 = LT1(d, 3);
+    return __byte_perm(__byte_perm(e0, e1, 0x3250u), __byte_perm(e2, e3, 0x7210u), 0x7610u) ^ k;
+}
+
+// Rounds 3..NR on a state that already went through rounds 0..2.
+template <int NR>
+__device__ __forceinline__ uint4 aes_rounds_from3(const uint8_t *t01, const uint8_t *t23, const LaneConst &L,
+                                                  uint32_t s0, uint32_t s1, uint32_t s2, uint32_t s3,
+                                                  const uint32_t *rk)
+{
 #pragma unroll
-    for (int r = 1; r < NR; r++) {
-        const uint32_t n0 = lds32(t01, TADDR(s0, 0, L.cA)) ^ lds32(t01, TADDR(s1, 1, L.cB)) ^
-                            lds32(t23, TADDR(s2, 2, L.cA)) ^ lds32(t23, TADDR(s3, 3, L.cB)) ^ rk[4 * r + 0];
-        const uint32_t n1 = lds32(t01, TADDR(s1, 0, L.cA)) ^ lds32(t01, TADDR(s2, 1, L.cB)) ^
-                            lds32(t23, TADDR(s3, 2, L.cA)) ^ lds32(t23, TADDR(s0, 3, L.cB)) ^ rk[4 * r + 1];
-        const uint32_t n2 = lds32(t01, TADDR(s2, 0, L.cA)) ^ lds32(t01, TADDR(s3, 1, L.cB)) ^
-                            lds32(t23, TADDR(s0, 2, L.cA)) ^ lds32(t23, TADDR(s1, 3, L.cB)) ^ rk[4 * r + 2];
-        const uint32_t n3 = lds32(t01, TADDR(s3, 0, L.cA)) ^ lds32(t01, TADDR(s0, 1, L.cB)) ^
-                            lds32(t23, TADDR(s1, 2, L.cA)) ^ lds32(t23, TADDR(s2, 3, L.cB)) ^ rk[4 * r + 3];
-        s0 = n0; s1 = n1; s2 = n2; s3 = n3;
-    }
-    // Final round: SubBytes + ShiftRows + AddRoundKey.  S[v] is byte 0 of
-    // T2[v], byte 1 of T3[v], byte 2 of T0[v] and byte 3 of T1[v].
+    for (int r = 3; r < NR; r++) aes_round(t01, t23, L, s0, s1, s2, s3, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
     uint4 o;
-#define LAST_COL(OUT, a, b, c, d, RK)                                                  \
-    {                                                                                   \
-        const uint32_t e0 = lds32(t23, TADDR(a, 0, L.cA));                              \
-        const uint32_t e1 = lds32(t23, TADDR(b, 1, L.cB));                              \
-        const uint32_t e2 = lds32(t01, TADDR(c, 2, L.cA));                              \
-        const uint32_t e3 = lds32(t01, TADDR(d, 3, L.cB));                              \
-        OUT = __byte_perm(__byte_perm(e0, e1, 0x3250u), __byte_perm(e2, e3, 0x7210u), 0x7610u) ^ (RK); \
-    }
-    LAST_COL(o.x, s0, s1, s2, s3, rk[4 * NR + 0]);
-    LAST_COL(o.y, s1, s2, s3, s0, rk[4 * NR + 1]);
-    LAST_COL(o.z, s2, s3, s0, s1, rk[4 * NR + 2]);
-    LAST_COL(o.w, s3, s0, s1, s2, rk[4 * NR + 3]);
-#undef LAST_COL
+    o.x = aes_last_col(t01, t23, L, s0, s1, s2, s3, rk[4 * NR + 0]);
+    o.y = aes_last_col(t01, t23, L, s1, s2, s3, s0, rk[4 * NR + 1]);
+    o.z = aes_last_col(t01, t23, L, s2, s3, s0, s1, rk[4 * NR + 2]);
+    o.w = aes_last_col(t01, t23, L, s3, s0, s1, s2, rk[4 * NR + 3]);
     return o;
 }
 
@@ -335,13 +340,40 @@ __device__ __forceinline__ void store_partial(uint8_t *dst, const uint4 &v, uint
     for (uint32_t b = 0; b < nbytes; b++) dst[b] = (uint8_t)(m[b >> 2] >> (8 * (b & 3)));
 }
 
+__device__ __forceinline__ uint4 keep_bytes(const uint4 &v, uint32_t nbytes)
+{
+    uint32_t m[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const uint32_t lo = 4u * i;
+        if (nbytes <= lo) m[i] = 0u;
+        else if (nbytes < lo + 4) m[i] &= (1u << (8 * (nbytes - lo))) - 1u;
+    }
+    return make_uint4(m[0], m[1], m[2], m[3]);
+}
+
+// KF.  Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C are
+// aligned to its end (the first tile is the short one and is treated as
+// left-padded with zero blocks).  Warp w of the CTA owns segment w of the
+// tile (S = tile/16 blocks).  On whole-payload segments the warp walks
+// windows of 32 counters aligned to multiples of 32, so a window never
+// crosses a 256-counter group: rounds 1 and 2 of AES then need only the
+// lookups that depend on the counter's low byte (counter-mode caching; the
+// rest are per-group constants computed once per 256 counters).  Lane l
+// chains the l-th block of every window through acc <- acc*H^32 xor X and
+// closes the chain with H^e, e = distance of its last block from the
+// segment end; the warp's partial then moves to the tile end with
+// H^((15-w)*S).
 template <int NR>
 __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
+    const uint32_t lane = tid & 31;
     const int warp = tid >> 5;
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    const KeyMat *km = p.km;
 
     // Stage the replicated round tables and this key's GHASH table.
     {
@@ -351,101 +383,162 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
             const int region = w >> 14, v = (w >> 6) & 255, odd = (w >> 5) & 1;
             s32[w] = __ldg(&tt[(2 * region + odd) * 256 + v]);
         }
-        const uint4 *g = p.km->gtab;
+        const uint4 *g = km->gtab;
         uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
         for (int i = tid; i < GTAB_ENTRIES; i += KF_THREADS) sg[i] = __ldg(&g[i]);
     }
+    const uint32_t tile_log2 = p.tile_log2;
+    const int64_t seg_blocks = (int64_t)1 << (tile_log2 - KF_LOG2_WARPS);
+    gf128 *segf = reinterpret_cast<gf128 *>(smem + SM_SEGF);
+    if (lane == 0) {
+        // H^((15-w) * S): moves warp w's segment partial to the tile end.
+        gf128 f;
+        f.w[0] = 0x80000000u; f.w[1] = f.w[2] = f.w[3] = 0u;
+        const int steps = KF_WARPS - 1 - warp;
+        for (int b = 0; b < KF_LOG2_WARPS; b++)
+            if ((steps >> b) & 1) f = gf_mul(f, km->h2k[tile_log2 - KF_LOG2_WARPS + b]);
+        segf[warp] = f;
+    }
     uint32_t rk[4 * (NR + 1)];
 #pragma unroll
-    for (int i = 0; i < 4 * (NR + 1); i++) rk[i] = __ldg(&p.km->rk[i]);
-    const uint32_t s0 = __ldg(&p.mm->j0[0]) ^ rk[0];
-    const uint32_t s1 = __ldg(&p.mm->j0[1]) ^ rk[1];
-    const uint32_t s2 = __ldg(&p.mm->j0[2]) ^ rk[2];
+    for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&km->rk[i]);
+    const uint32_t j0w0 = __ldg(&p.mm->j0[0]), j0w1 = __ldg(&p.mm->j0[1]), j0w2 = __ldg(&p.mm->j0[2]);
     const uint32_t ctr0 = bswap32(__ldg(&p.mm->j0[3]));
-    const LaneConst L = make_lane_const(lane);
+    const LaneConst L = make_lane_const((int)lane);
     gf128 *red = reinterpret_cast<gf128 *>(smem + SM_RED);
     const uint64_t a_blocks = p.a_blocks;
     const uint64_t n_full = p.n_full;
     const bool dec = p.decrypt != 0;
     __syncthreads();
 
-    for (uint64_t tile = blockIdx.x; tile < p.K; tile += gridDim.x) {
-        const uint64_t tile_blocks = 1ull << p.tile_log2;
-        const uint64_t tend = p.M - ((p.K - 1 - tile) << p.tile_log2);
-        const uint64_t tbeg = (tend > tile_blocks) ? tend - tile_blocks : 0ull;
-        const uint32_t tlen = (uint32_t)(tend - tbeg);
-        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+    // Message constants of round 1: everything except the lookups of
+    // counter bytes 12..15 (K0 still misses byte 15, K1..K3 bytes 14, 13, 12).
+    const uint32_t x0 = j0w0 ^ __ldg(&km->rk[0]);
+    const uint32_t x1 = j0w1 ^ __ldg(&km->rk[1]);
+    const uint32_t x2 = j0w2 ^ __ldg(&km->rk[2]);
+    const uint32_t rk3 = __ldg(&km->rk[3]);
+    const uint32_t K0 = LT0(x0, 0) ^ LT1(x1, 1) ^ LT2(x2, 2) ^ __ldg(&km->rk[4]);
+    const uint32_t K1 = LT0(x1, 0) ^ LT1(x2, 1) ^ LT3(x0, 3) ^ __ldg(&km->rk[5]);
+    const uint32_t K2 = LT0(x2, 0) ^ LT2(x0, 2) ^ LT3(x1, 3) ^ __ldg(&km->rk[6]);
+    const uint32_t K3 = LT1(x0, 1) ^ LT2(x1, 2) ^ LT3(x2, 3) ^ __ldg(&km->rk[7]);
+    const uint32_t k15 = rk3 >> 24;
+    uint32_t grp = 0xFFFFFFFFu, G0 = 0, G1 = 0, G2 = 0, G3 = 0;
 
-        if (tbeg >= a_blocks && tend <= a_blocks + n_full) {
-            // Whole payload blocks only.
-            const uint64_t j_base = tbeg - a_blocks;
-            const uint4 *in = reinterpret_cast<const uint4 *>(p.in) + j_base;
-            uint4 *out = reinterpret_cast<uint4 *>(p.out) + j_base;
-            for (uint32_t sl = tid; sl < tlen; sl += KF_THREADS) {
-                const uint4 din = __ldcs(in + sl);
-                const uint32_t ctr = ctr0 + 1u + (uint32_t)(j_base + sl);
-                uint4 ks = aes_ctr_block<NR>(smem, rk, s0, s1, s2, bswap32(ctr), L);
-                ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                __stcs(out + sl, ks);
-                uint4 m = ghash_mul_table(smem, acc, L);
-                xor4(m, dec ? din : ks);
-                acc = m;
-            }
-        } else {
-            // Tiles that touch the AAD or the final partial block.
-            for (uint32_t sl = tid; sl < tlen; sl += KF_THREADS) {
-                const uint64_t s = tbeg + sl;
-                uint4 x;
-                if (s < a_blocks) {
-                    const uint64_t off = s * 16u;
-                    const uint64_t rem = p.aad_len - off;
-                    const uint8_t *src = p.aad + off;
-                    if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
-                        x = *reinterpret_cast<const uint4 *>(src);
-                    else
-                        x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
-                } else {
-                    const uint64_t j = s - a_blocks;
-                    const uint32_t ctr = ctr0 + 1u + (uint32_t)j;
-                    uint4 ks = aes_ctr_block<NR>(smem, rk, s0, s1, s2, bswap32(ctr), L);
-                    if (j < n_full) {
-                        const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(p.in) + j);
+    for (uint64_t tile = blockIdx.x; tile < p.K; tile += gridDim.x) {
+        const int64_t tend = (int64_t)p.M - (int64_t)((p.K - 1 - tile) << tile_log2);
+        const int64_t tv_lo = tend - ((int64_t)1 << tile_log2);
+        const int64_t seg_hi = tv_lo + (int64_t)(warp + 1) * seg_blocks;
+        int64_t seg_lo = tv_lo + (int64_t)warp * seg_blocks;
+        if (seg_lo < 0) seg_lo = 0;
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t dlast = 0;
+        bool have = false;
+        uint32_t seg_len = 0;
+
+        if (seg_hi > seg_lo) {
+            seg_len = (uint32_t)(seg_hi - seg_lo);
+            if ((uint64_t)seg_lo >= a_blocks && (uint64_t)seg_hi <= a_blocks + n_full) {
+                // Whole payload blocks: counter-aligned windows of 32.
+                const uint64_t j_lo = (uint64_t)seg_lo - a_blocks;
+                const uint32_t c_lo = ctr0 + 1u + (uint32_t)j_lo;
+                const uint32_t W0 = c_lo & ~31u;
+                const uint32_t nwin = (seg_len + (c_lo & 31u) + 31u) >> 5;
+                const uint4 *in = reinterpret_cast<const uint4 *>(p.in) + j_lo;
+                uint4 *out = reinterpret_cast<uint4 *>(p.out) + j_lo;
+                for (uint32_t wi = 0; wi < nwin; wi++) {
+                    const uint32_t W = W0 + (wi << 5);
+                    const uint32_t d = W + lane - c_lo;
+                    const bool active = d < seg_len;
+                    uint4 din = make_uint4(0u, 0u, 0u, 0u);
+                    if (active) din = __ldcs(in + d);
+                    if ((W >> 8) != grp) {
+                        // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
+                        grp = W >> 8;
+                        const uint32_t x3g = bswap32(W) ^ rk3;
+                        const uint32_t u1 = K1 ^ LT2(x3g, 2);
+                        const uint32_t u2 = K2 ^ LT1(x3g, 1);
+                        const uint32_t u3 = K3 ^ LT0(x3g, 0);
+                        G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
+                        G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
+                        G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
+                        G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
+                    }
+                    // Round 1 column 0 (the only column that sees counter byte 15),
+                    // then round 2 (one varying lookup per column).
+                    const uint32_t x15 = ((W & 0xE0u) | lane) ^ k15;
+                    const uint32_t v0 = K0 ^ LT3(x15, 0);
+                    uint4 ks = aes_rounds_from3<NR>(t01, t23, L, G0 ^ LT0(v0, 0), G1 ^ LT3(v0, 3),
+                                                    G2 ^ LT2(v0, 2), G3 ^ LT1(v0, 1), rk);
+                    if (active) {
                         ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                        __stcs(reinterpret_cast<uint4 *>(p.out) + j, ks);
-                        x = dec ? din : ks;
-                    } else {
-                        const uint32_t nb = (uint32_t)(p.len - j * 16u);
-                        const uint4 din = load_partial(p.in + j * 16u, nb);
-                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                        // keep only the nb valid bytes of the ciphertext block
-                        uint4 c = load_partial(reinterpret_cast<const uint8_t *>(&ks), nb);
-                        store_partial(p.out + j * 16u, c, nb);
-                        x = dec ? din : c;
+                        __stcs(out + d, ks);
+                        uint4 m = ghash_mul_table(smem, acc, L);
+                        xor4(m, dec ? din : ks);
+                        acc = m;
+                        dlast = d;
+                        have = true;
                     }
                 }
-                uint4 m = ghash_mul_table(smem, acc, L);
-                xor4(m, x);
-                acc = m;
+            } else {
+                // Segments that touch the AAD or the final partial block.
+                uint32_t rlo[12];
+#pragma unroll
+                for (int i = 0; i < 12; i++) rlo[i] = __ldg(&km->rk[i]);
+                for (uint32_t q = lane; q < seg_len; q += 32) {
+                    const uint64_t s = (uint64_t)seg_lo + q;
+                    uint4 x;
+                    if (s < a_blocks) {
+                        const uint64_t off = s * 16u;
+                        const uint64_t rem = p.aad_len - off;
+                        const uint8_t *src = p.aad + off;
+                        if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
+                            x = *reinterpret_cast<const uint4 *>(src);
+                        else
+                            x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
+                    } else {
+                        const uint64_t j = s - a_blocks;
+                        const uint32_t ctr = ctr0 + 1u + (uint32_t)j;
+                        uint32_t s0 = j0w0 ^ rlo[0], s1 = j0w1 ^ rlo[1], s2 = j0w2 ^ rlo[2];
+                        uint32_t s3 = bswap32(ctr) ^ rlo[3];
+                        aes_round(t01, t23, L, s0, s1, s2, s3, rlo[4], rlo[5], rlo[6], rlo[7]);
+                        aes_round(t01, t23, L, s0, s1, s2, s3, rlo[8], rlo[9], rlo[10], rlo[11]);
+                        uint4 ks = aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
+                        if (j < n_full) {
+                            const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(p.in) + j);
+                            ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                            __stcs(reinterpret_cast<uint4 *>(p.out) + j, ks);
+                            x = dec ? din : ks;
+                        } else {
+                            const uint32_t nb = (uint32_t)(p.len - j * 16u);
+                            const uint4 din = load_partial(p.in + j * 16u, nb);
+                            ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                            const uint4 c = keep_bytes(ks, nb);
+                            store_partial(p.out + j * 16u, c, nb);
+                            x = dec ? din : c;
+                        }
+                    }
+                    uint4 m = ghash_mul_table(smem, acc, L);
+                    xor4(m, x);
+                    acc = m;
+                    dlast = q;
+                    have = true;
+                }
             }
         }
 
-        // Close this thread's chain: its last block sits e blocks before the
-        // tile end, so the chain value is multiplied by H^e (1 <= e <= T).
+        // Close the lane's chain (its last block is e = seg_len - dlast blocks
+        // before the segment end, 1 <= e <= 32), reduce the warp, move the
+        // warp's partial to the tile end, reduce the CTA.
         gf128 z = gf_zero();
-        if ((uint32_t)tid < tlen) {
-            const uint32_t q = (tlen - tid + KF_THREADS - 1) / KF_THREADS;
-            const uint32_t e = tlen - tid - KF_THREADS * (q - 1);
-            z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), p.km->hpow[e - 1]);
-        }
-        // XOR-reduce the CTA's contributions into the tile partial.
+        if (have) z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), km->hpow[seg_len - dlast - 1]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
             for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
-        if (lane == 0) red[warp] = z;
+        if (lane == 0) red[warp] = (warp == KF_WARPS - 1) ? z : gf_mul(z, segf[warp]);
         __syncthreads();
         if (warp == 0) {
-            z = (lane < KF_THREADS / 32) ? red[lane] : gf_zero();
+            z = (lane < KF_WARPS) ? red[lane] : gf_zero();
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -455,6 +548,10 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
         __syncthreads();
     }
 }
+#undef LT0
+#undef LT1
+#undef LT2
+#undef LT3
 
 // ---------------------------------------------------------------------
 // KC: log-depth combine + tag (one CTA)
