@@ -127,6 +127,46 @@ int gcm_profile_enable(gcm_ctx *ctx, int enable);
 int gcm_profile_read(gcm_ctx *ctx, int reset, double *fused_ms, uint64_t *fused_launches,
                      uint64_t *fused_bytes, uint64_t *launches);
 
+/* ---------------------------------------------------------------- */
+/* Allocation-free encryption (the paper has no counterpart)        */
+/* ---------------------------------------------------------------- */
+
+/* GCM-AE like gcm_encrypt in device mode, but without a context and without
+ * allocating any device memory.  It is meant for callers that cannot call
+ * cudaMalloc at call time: a process whose device memory is already handed
+ * out by another allocator (for example a framework's caching pool that owns
+ * almost all of HBM), or a latency-critical loop that must not risk the
+ * implicit device-wide synchronisation that cudaMalloc/cudaFree can cause.
+ *
+ * All scratch (round tables, key material, tile partials) lives in one
+ * fixed device array of about 268 KiB inside the library, which every GPU
+ * that loads the library keeps until the process exits.  The caller still
+ * passes its own buffers: aad, pt, ct and tag are DEVICE pointers (pt/ct
+ * 16-byte aligned, ct may equal pt); key and iv are host pointers.
+ *
+ * Limits: payload + AAD of at most 8 GiB (2^29 blocks) and IVs of at most
+ * 256 bytes; larger requests return GCM_ERR_LENGTH_LIMIT without touching
+ * the GPU.  Works on the caller's current CUDA device.
+ *
+ * The first call on each device sets that device up (finds the array's
+ * device address, builds the round tables in it) and synchronises `stream`;
+ * make that first call before any stream capture.  Later calls only enqueue
+ * work on `stream` and return.
+ *
+ * Every call shares the one array and the array keeps the last call's
+ * contents, so calls whose work overlaps on the GPU (e.g. issued on two
+ * streams without ordering) race and can produce wrong tags; order them on
+ * one stream.  No part of the array needs clearing between calls: each call
+ * writes everything it reads.  Error text: gcm_noalloc_last_error(). */
+int gcm_encrypt_noalloc(const uint8_t *key, size_t key_len,
+                        const uint8_t *iv, size_t iv_len,
+                        const uint8_t *aad, size_t aad_len,
+                        const uint8_t *pt, size_t len, uint8_t *ct, uint8_t *tag,
+                        void *stream);
+
+/* Message of the last gcm_encrypt_noalloc error on the calling thread. */
+const char *gcm_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,8 @@ SIGNATURES = {
     "gcm_profile_read": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]),
+    "gcm_encrypt_noalloc": (ctypes.c_int, [_VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP]),
+    "gcm_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 
@@ -121,3 +123,16 @@ def gcm_profile_read(ctx, reset: bool = False):
     check(lib.gcm_profile_read(ctx, 1 if reset else 0, ctypes.byref(ms), ctypes.byref(nl), ctypes.byref(nb),
                                ctypes.byref(la)))
     return {"fused_ms": ms.value, "fused_launches": nl.value, "fused_bytes": nb.value, "launches": la.value}
+
+
+def gcm_encrypt_noalloc(key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, pt_ptr, length, ct_ptr, tag_ptr,
+                        stream) -> int:
+    """Raw call of the allocation-free encryption (device pointers for aad,
+    pt, ct, tag; host pointers for key and iv).  Returns the status code."""
+    return lib.gcm_encrypt_noalloc(key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, pt_ptr, length, ct_ptr,
+                                   tag_ptr, stream)
+
+
+def noalloc_last_error() -> str:
+    msg = lib.gcm_noalloc_last_error()
+    return msg.decode("utf-8", "replace") if msg else ""
