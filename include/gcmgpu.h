@@ -128,6 +128,89 @@ int gcm_profile_read(gcm_ctx *ctx, int reset, double *fused_ms, uint64_t *fused_
                      uint64_t *fused_bytes, uint64_t *launches);
 
 /* ---------------------------------------------------------------- */
+/* FITS wrapper (Sec. 3.2.2-3.2.3; Table "Core functions")          */
+/* ---------------------------------------------------------------- */
+
+/* Which bytes authenticate the data unit.
+ *   GFC_AAD_HEADER     : the header records exactly as in the file (every
+ *                        2880-byte record through the one holding END,
+ *                        blank padding included); the header stays in clear.
+ *   GFC_AAD_STRUCTURAL : the paper's AAD_Data = NONCE || Serialize(BITPIX)
+ *                        || Serialize(NAXIS) || Serialize(NAXIS1) || ... with
+ *                        Serialize = strict ASCII decimal and no separators
+ *                        (Sec. 3.2.3). */
+typedef enum {
+    GFC_AAD_HEADER = 0,
+    GFC_AAD_STRUCTURAL = 1
+} gfc_aad_mode;
+
+#define GFC_MAX_AXES 999
+
+/* The FITS layout of a single-HDU file, from its header (FITS standard:
+ * 2880-byte records of 80-character cards). */
+typedef struct {
+    size_t header_bytes;      /* records up to and including the END record */
+    size_t data_bytes;        /* |BITPIX|/8 * NAXIS1 * ... * NAXISn (0 if NAXIS = 0) */
+    size_t data_padded_bytes; /* data_bytes rounded up to whole 2880-byte records */
+    int bitpix;
+    int naxis;
+    int64_t naxes[16];        /* the first 16 axis lengths */
+} gfc_layout;
+
+/* Parses the header at `fits` (host memory, `len` bytes available).
+ * Returns GCM_ERR_INVALID_ARG if no END card is found, or if SIMPLE,
+ * BITPIX or NAXISn are missing or malformed. */
+int gfc_fits_layout(const uint8_t *fits, size_t len, gfc_layout *out);
+
+/* The paper's FitsOperationResult (Table "Core functions").
+ * data_buffer / buffer_size: the processed file (header records in clear,
+ *   then the processed record-padded data unit); owned by the library until
+ *   gfc_result_free; in device memory when the call was made with
+ *   GCM_MEM_DEVICE, else in pinned host memory.
+ * error_code: 0, or the negative gcm_status of the call.
+ * warning_code: 0 full access; 2 payload suppressed (tag mismatch: the data
+ *   unit in data_buffer is zero-filled and the header is returned as is).
+ * error_message: text of the failure ("" on success). */
+typedef struct {
+    uint8_t *data_buffer;
+    size_t buffer_size;
+    int error_code;
+    int warning_code;
+    char error_message[200];
+    int mem;
+    void *stream;
+} gfc_result;
+
+/* Encrypts the data unit of a single-HDU FITS file and authenticates it
+ * together with the AAD chosen by aad_mode.  iv12 is a 12-byte IV, or NULL
+ * to draw one from the operating system's entropy source (Sec. 3.2.2:
+ * 96-bit nonces from /dev/urandom); the IV used is written to iv_out (host,
+ * 12 bytes) and the tag to tag_out (host, 16 bytes).  fits points to
+ * fits_len bytes in the memory space given by mem (device pointers must be
+ * 16-byte aligned).  A file whose data unit lacks its final padding is
+ * zero-padded; bytes after the padded data unit (further HDUs) are
+ * rejected with GCM_ERR_INVALID_ARG.  Returns the status also stored in
+ * out->error_code; on success out holds the encrypted file. */
+int gfc_fits_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+                     const uint8_t *fits, size_t fits_len, const uint8_t *iv12,
+                     uint8_t *iv_out, uint8_t *tag_out, int aad_mode, int mem,
+                     void *stream, gfc_result *out);
+
+/* Decrypts and verifies a file produced by gfc_fits_encrypt (the paper's
+ * gfc_decrypt_frame with the validation gate, Sec. 3.3.2 item 4, and the
+ * payload suppression of Sec. 4.2).  iv12 and tag are host pointers.  On a
+ * tag mismatch the call returns GCM_ERR_AUTH, out->warning_code is 2 and the
+ * data unit of out->data_buffer is all zero bytes. */
+int gfc_fits_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+                            const uint8_t *fits_enc, size_t len, const uint8_t *iv12,
+                            const uint8_t *tag, int aad_mode, int mem, void *stream,
+                            gfc_result *out);
+
+/* Releases out->data_buffer (mirrors the teardown side of the paper's API).
+ * Safe on a zeroed or already released result. */
+void gfc_result_free(gcm_ctx *ctx, gfc_result *res);
+
+/* ---------------------------------------------------------------- */
 /* Allocation-free encryption (the paper has no counterpart)        */
 /* ---------------------------------------------------------------- */
 

@@ -38,6 +38,22 @@ STATUS_NAMES = {
     GCM_ERR_BUSY: "GCM_ERR_BUSY",
 }
 
+GFC_AAD_HEADER = 0
+GFC_AAD_STRUCTURAL = 1
+
+
+class GfcLayout(ctypes.Structure):
+    _fields_ = [("header_bytes", ctypes.c_size_t), ("data_bytes", ctypes.c_size_t),
+                ("data_padded_bytes", ctypes.c_size_t), ("bitpix", ctypes.c_int), ("naxis", ctypes.c_int),
+                ("naxes", ctypes.c_int64 * 16)]
+
+
+class GfcResult(ctypes.Structure):
+    _fields_ = [("data_buffer", ctypes.c_void_p), ("buffer_size", ctypes.c_size_t), ("error_code", ctypes.c_int),
+                ("warning_code", ctypes.c_int), ("error_message", ctypes.c_char * 200), ("mem", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _VP = ctypes.c_void_p
 _SZ = ctypes.c_size_t
@@ -52,6 +68,12 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_encrypt_noalloc": (ctypes.c_int, [_VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP]),
+    "gfc_fits_layout": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(GfcLayout)]),
+    "gfc_fits_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP,
+                                        ctypes.POINTER(GfcResult)]),
+    "gfc_fits_decrypt_verify": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                               _VP, ctypes.POINTER(GfcResult)]),
+    "gfc_result_free": (None, [_VP, ctypes.POINTER(GfcResult)]),
     "gcm_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
@@ -136,3 +158,10 @@ def gcm_encrypt_noalloc(key_ptr, key_len, iv_ptr, iv_len, aad_ptr, aad_len, pt_p
 def noalloc_last_error() -> str:
     msg = lib.gcm_noalloc_last_error()
     return msg.decode("utf-8", "replace") if msg else ""
+
+
+def gfc_fits_layout(fits: bytes) -> GfcLayout:
+    buf = ctypes.create_string_buffer(bytes(fits), max(1, len(fits)))
+    out = GfcLayout()
+    check(lib.gfc_fits_layout(ctypes.addressof(buf), len(fits), ctypes.byref(out)))
+    return out

@@ -10,13 +10,30 @@ from __future__ import annotations
 import ctypes
 from typing import Optional, Tuple
 
-from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GcmError, check,
-                      gcm_ctx_create, gcm_ctx_destroy, gcm_decrypt_verify, gcm_encrypt, last_error)
+from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GFC_AAD_HEADER, GFC_AAD_STRUCTURAL,
+                      GcmError, GfcResult, check, gcm_ctx_create, gcm_ctx_destroy, gcm_decrypt_verify, gcm_encrypt,
+                      last_error, lib)
 
 __all__ = [
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
     "gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "last_error",
+    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL",
 ]
+
+
+class FitsResult:
+    """A processed FITS file (the paper's FitsOperationResult): ``data`` is a
+    uint8 CUDA tensor (device calls) or numpy array (host calls) holding the
+    header in clear and the processed data unit; ``warning_code`` is 2 when
+    the payload was suppressed after a tag mismatch."""
+
+    def __init__(self, data, error_code: int, warning_code: int, message: str, iv: bytes = b"", tag: bytes = b""):
+        self.data = data
+        self.error_code = error_code
+        self.warning_code = warning_code
+        self.message = message
+        self.iv = iv
+        self.tag = tag
 
 
 def _host_buf(data) -> Tuple[int, int, object]:
@@ -158,3 +175,121 @@ class Context:
             raise ValueError("bad buffer sizes")
         check(gcm_decrypt_verify(self.handle, kp, kl, ip, il, ap, al, cp, cl, tp, pp, GCM_MEM_HOST, stream))
         return pt
+
+    # -- FITS files (header in clear, data unit encrypted) ------------------
+    def _fits_common(self, decrypt, key, fits, iv, tag, aad_mode, stream):
+        import numpy as np
+
+        kp, kl, kk = _host_buf(key)
+        device = hasattr(fits, "is_cuda") and fits.is_cuda
+        if device:
+            fp, fl = _dev_buf(fits)
+            mem, st = GCM_MEM_DEVICE, _stream_handle(stream)
+        else:
+            fp, fl, fk = _host_buf(fits)
+            mem, st = GCM_MEM_HOST, (stream or 0)
+        res = GfcResult()
+        iv_out = ctypes.create_string_buffer(12)
+        tag_out = ctypes.create_string_buffer(16)
+        ivb = ctypes.create_string_buffer(bytes(iv), 12) if iv is not None else None
+        if decrypt:
+            tb = ctypes.create_string_buffer(bytes(tag), 16)
+            rc = lib.gfc_fits_decrypt_verify(self.handle, kp, kl, fp, fl, ctypes.addressof(ivb),
+                                             ctypes.addressof(tb), aad_mode, mem, st, ctypes.byref(res))
+        else:
+            rc = lib.gfc_fits_encrypt(self.handle, kp, kl, fp, fl, ctypes.addressof(ivb) if ivb is not None else None,
+                                      ctypes.addressof(iv_out), ctypes.addressof(tag_out), aad_mode, mem, st,
+                                      ctypes.byref(res))
+        msg = res.error_message.decode("utf-8", "replace")
+        data = None
+        if res.data_buffer:
+            n = res.buffer_size
+            if device:
+                data = _dev_tensor_copy(res.data_buffer, n, fits.device)
+            else:
+                data = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(res.data_buffer)).copy()
+            lib.gfc_result_free(self.handle, ctypes.byref(res))
+        if rc not in (GCM_OK, GCM_ERR_AUTH):
+            raise GcmError(rc, msg)
+        return FitsResult(data, rc, res.warning_code, msg, iv_out.raw if not decrypt else bytes(iv),
+                          tag_out.raw if not decrypt else bytes(tag))
+
+    def fits_encrypt_raw(self, key: bytes, fits, iv: bytes, aad_mode: int = GFC_AAD_HEADER, stream=None):
+        """gfc_fits_encrypt on a CUDA tensor without copying the result: returns
+        (GfcResult, tag).  The result buffer belongs to the library until
+        ``release(result)``."""
+        kp, kl, kk = _host_buf(key)
+        fp, fl = _dev_buf(fits)
+        res = GfcResult()
+        ivb = ctypes.create_string_buffer(bytes(iv), 12)
+        iv_out, tag_out = ctypes.create_string_buffer(12), ctypes.create_string_buffer(16)
+        rc = lib.gfc_fits_encrypt(self.handle, kp, kl, fp, fl, ctypes.addressof(ivb), ctypes.addressof(iv_out),
+                                  ctypes.addressof(tag_out), aad_mode, GCM_MEM_DEVICE, _stream_handle(stream),
+                                  ctypes.byref(res))
+        if rc != GCM_OK:
+            raise GcmError(rc, res.error_message.decode("utf-8", "replace"))
+        return res, tag_out.raw
+
+    def fits_decrypt_verify_raw(self, key: bytes, enc_ptr: int, enc_len: int, iv: bytes, tag: bytes,
+                                aad_mode: int = GFC_AAD_HEADER, stream=None):
+        """gfc_fits_decrypt_verify on a device buffer (e.g. a raw encryption
+        result) without copying: returns the GfcResult (raises on errors other
+        than a tag mismatch)."""
+        kp, kl, kk = _host_buf(key)
+        res = GfcResult()
+        ivb = ctypes.create_string_buffer(bytes(iv), 12)
+        tb = ctypes.create_string_buffer(bytes(tag), 16)
+        rc = lib.gfc_fits_decrypt_verify(self.handle, kp, kl, enc_ptr, enc_len, ctypes.addressof(ivb),
+                                         ctypes.addressof(tb), aad_mode, GCM_MEM_DEVICE, _stream_handle(stream),
+                                         ctypes.byref(res))
+        if rc not in (GCM_OK, GCM_ERR_AUTH):
+            raise GcmError(rc, res.error_message.decode("utf-8", "replace"))
+        return res
+
+    def release(self, res) -> None:
+        """gfc_result_free for a raw result."""
+        lib.gfc_result_free(self.handle, ctypes.byref(res))
+
+    @staticmethod
+    def result_view(res, offset: int = 0, length: Optional[int] = None, device=None):
+        """A uint8 tensor viewing (not copying) a raw device result."""
+        import torch
+
+        n = (res.buffer_size - offset) if length is None else length
+        return torch.as_tensor(_DevView(res.data_buffer + offset, n), device=device or "cuda")
+
+    def fits_encrypt(self, key: bytes, fits, iv: Optional[bytes] = None, aad_mode: int = GFC_AAD_HEADER,
+                     stream=None) -> "FitsResult":
+        """gfc_fits_encrypt.  ``fits`` is bytes/numpy (host) or a CUDA uint8
+        tensor (device).  iv=None draws a random 96-bit IV."""
+        return self._fits_common(False, key, fits, iv, None, aad_mode, stream)
+
+    def fits_decrypt_verify(self, key: bytes, fits_enc, iv: bytes, tag: bytes, aad_mode: int = GFC_AAD_HEADER,
+                            stream=None) -> "FitsResult":
+        """gfc_fits_decrypt_verify.  A tag mismatch does not raise: the
+        result has error_code GCM_ERR_AUTH, warning_code 2 and a zeroed data
+        unit (payload suppression)."""
+        return self._fits_common(True, key, fits_enc, iv, tag, aad_mode, stream)
+
+
+class _Raw:
+    pass
+
+
+class _DevView:
+    """Exposes a library-owned device buffer to torch (CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "|u1", "data": (ptr, False), "version": 3,
+                                         "strides": None}
+
+
+def _dev_tensor_copy(ptr: int, n: int, device):
+    """Copies n bytes at a library-owned device pointer into a new tensor."""
+    import torch
+
+    torch.cuda.synchronize(device)
+    view = torch.as_tensor(_DevView(ptr, n), device=device)
+    out = view.clone()
+    torch.cuda.synchronize(device)
+    return out

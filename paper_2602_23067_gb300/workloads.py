@@ -66,7 +66,8 @@ def fits_header(seed: int, bitpix: int, naxes: List[int], ncards: int = 36) -> b
         _card("EXTEND", True),
         _card("CTYPE1", "RA---TAN"), _card("CTYPE2", "DEC--TAN"),
         _card("CRVAL1", ra), _card("CRVAL2", dec),
-        _card("CRPIX1", float(naxes[0]) / 2 + 0.5), _card("CRPIX2", float(naxes[-1]) / 2 + 0.5),
+        _card("CRPIX1", float(naxes[0] if naxes else 1) / 2 + 0.5),
+        _card("CRPIX2", float(naxes[-1] if naxes else 1) / 2 + 0.5),
         _card("CD1_1", -scale), _card("CD1_2", 0.0), _card("CD2_1", 0.0), _card("CD2_2", scale),
         _card("CUNIT1", "deg"), _card("CUNIT2", "deg"),
         _card("RADESYS", "ICRS"), _card("EQUINOX", 2000.0),
