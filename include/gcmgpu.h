@@ -88,7 +88,8 @@ const char *gcm_last_error(void);
  *   pt/len      : plaintext;  ct receives len bytes of ciphertext.
  *   tag         : receives the 16-byte tag T = E_K(J0) xor GHASH_H(A, C).
  * Device mode: returns once the work is enqueued on `stream`.
- * Host mode:   copies through device scratch and returns when done. */
+ * Host mode:   streams the buffers through device chunk buffers (see
+ *              gcm_batch) and returns when done; `stream` is not used. */
 int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                 const uint8_t *iv, size_t iv_len,
                 const uint8_t *aad, size_t aad_len,
@@ -107,6 +108,53 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                        const uint8_t *aad, size_t aad_len,
                        const uint8_t *ct, size_t len, const uint8_t *tag,
                        uint8_t *pt, int mem, void *stream);
+
+/* ---------------------------------------------------------------- */
+/* Many messages: batched device launch and streamed host catalogs   */
+/* ---------------------------------------------------------------- */
+
+/* One independent message.  key and iv are host pointers; aad, in, out and
+ * tag follow the mem argument of gcm_batch.  out may equal in.  For
+ * encryption tag receives the 16-byte tag, for decryption it holds the
+ * expected tag. */
+typedef struct {
+    const uint8_t *key;
+    size_t key_len;
+    const uint8_t *iv;
+    size_t iv_len;
+    const uint8_t *aad;
+    size_t aad_len;
+    const uint8_t *in;
+    uint8_t *out;
+    size_t len;
+    uint8_t *tag;
+} gcm_msg;
+
+/* Processes n independent messages (encrypt if decrypt == 0, else
+ * decrypt-verify) and returns when all are done.  status (host array of n)
+ * receives 0 or GCM_ERR_AUTH per message; the call returns GCM_OK if the
+ * batch ran (individual tag failures are only in status), or the first
+ * argument/CUDA error.  Outputs of messages whose tag failed are zero-filled.
+ *
+ * GCM_MEM_DEVICE: all messages go into ONE persistent launch that splits the
+ *   work into (message, tile) items taken from an atomic counter; each
+ *   message's GHASH partials are reduced across its tiles by the CTA that
+ *   finishes the message's last tile (no spin-waits).  Key setup for all
+ *   messages is one launch.  Messages of different key sizes mix freely.
+ * GCM_MEM_HOST: buffers (ideally pinned) are streamed through a ring of
+ *   device chunk buffers: host-to-device copies, the fused kernel and
+ *   device-to-host copies of successive chunks overlap on three streams
+ *   (the paper's asynchronous stream pipeline, Sec. 3.3.2), so catalogs
+ *   larger than device memory pass through a fixed device footprint.
+ * stream: the stream the device-mode launch is ordered on (host mode uses
+ *   the context's own streams). */
+int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
+              int32_t *status, int mem, void *stream);
+
+/* Host-mode streaming geometry: chunk_bytes of payload per chunk (rounded
+ * to whole tiles) and n_buffers device chunk buffers in the ring (>= 2).
+ * Defaults: 256 MiB and 3. */
+int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers);
 
 /* ---------------------------------------------------------------- */
 /* Measurement hooks (used by the benchmark; no counterpart in the  */

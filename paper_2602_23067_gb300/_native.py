@@ -54,6 +54,13 @@ class GfcResult(ctypes.Structure):
                 ("stream", ctypes.c_void_p)]
 
 
+class GcmMsg(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("key_len", ctypes.c_size_t), ("iv", ctypes.c_void_p),
+                ("iv_len", ctypes.c_size_t), ("aad", ctypes.c_void_p), ("aad_len", ctypes.c_size_t),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("len", ctypes.c_size_t),
+                ("tag", ctypes.c_void_p)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _VP = ctypes.c_void_p
 _SZ = ctypes.c_size_t
@@ -69,6 +76,9 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_encrypt_noalloc": (ctypes.c_int, [_VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP]),
     "gfc_fits_layout": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(GfcLayout)]),
+    "gcm_batch": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.c_int, _VP]),
+    "gcm_ctx_set_streaming": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
     "gfc_fits_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                         ctypes.POINTER(GfcResult)]),
     "gfc_fits_decrypt_verify": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, ctypes.c_int,

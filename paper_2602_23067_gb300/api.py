@@ -11,8 +11,8 @@ import ctypes
 from typing import Optional, Tuple
 
 from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GFC_AAD_HEADER, GFC_AAD_STRUCTURAL,
-                      GcmError, GfcResult, check, gcm_ctx_create, gcm_ctx_destroy, gcm_decrypt_verify, gcm_encrypt,
-                      last_error, lib)
+                      GcmError, GcmMsg, GfcResult, check, gcm_ctx_create, gcm_ctx_destroy, gcm_decrypt_verify,
+                      gcm_encrypt, last_error, lib)
 
 __all__ = [
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
@@ -175,6 +175,50 @@ class Context:
             raise ValueError("bad buffer sizes")
         check(gcm_decrypt_verify(self.handle, kp, kl, ip, il, ap, al, cp, cl, tp, pp, GCM_MEM_HOST, stream))
         return pt
+
+    # -- many messages (gcm_batch) ------------------------------------------
+    def set_streaming(self, chunk_bytes: int, n_buffers: int = 3) -> None:
+        check(lib.gcm_ctx_set_streaming(self.handle, chunk_bytes, n_buffers))
+
+    def batch(self, msgs, decrypt: bool = False, stream=None):
+        """gcm_batch over a list of dicts with keys key, iv (bytes) and aad,
+        inp, out, tag: CUDA tensors (device batch: one persistent launch) or
+        host buffers (numpy / pinned tensors: the streamed pipeline).  All
+        messages must live in the same memory space.  Returns the list of
+        per-message status codes (0 or GCM_ERR_AUTH)."""
+        n = len(msgs)
+        arr = (GcmMsg * max(1, n))()
+        keep = []
+        device = None
+        for i, m in enumerate(msgs):
+            kp, kl, kk = _host_buf(m["key"])
+            ip, il, ik = _host_buf(m["iv"])
+            keep += [kk, ik]
+            dev = hasattr(m["inp"], "is_cuda") and m["inp"].is_cuda
+            if device is None:
+                device = dev
+            elif device != dev:
+                raise ValueError("all messages of a batch must be in the same memory space")
+            if dev:
+                ap, al = _dev_buf(m.get("aad"))
+                pp, pl = _dev_buf(m["inp"])
+                op, ol = _dev_buf(m["out"])
+                tp, tl = _dev_buf(m["tag"])
+            else:
+                ap, al, ak = _host_buf(m.get("aad"))
+                pp, pl, pk = _host_buf(m["inp"])
+                op, ol, ok = _host_buf(m["out"])
+                tp, tl, tk = _host_buf(m["tag"])
+                keep += [ak, pk, ok, tk]
+            n_bytes = m.get("len", pl)
+            if ol < n_bytes or tl < 16:
+                raise ValueError("output or tag buffer too small")
+            arr[i] = GcmMsg(kp, kl, ip, il, ap or None, al, pp or None, op or None, n_bytes, tp)
+        status = (ctypes.c_int32 * max(1, n))()
+        mem = GCM_MEM_DEVICE if device else GCM_MEM_HOST
+        st = _stream_handle(stream) if device else 0
+        check(lib.gcm_batch(self.handle, arr, n, 1 if decrypt else 0, status, mem, st))
+        return [int(status[i]) for i in range(n)]
 
     # -- FITS files (header in clear, data unit encrypted) ------------------
     def _fits_common(self, decrypt, key, fits, iv, tag, aad_mode, stream):

@@ -75,7 +75,7 @@ cudaEvent_t take_event(gcm_ctx *ctx)
 
 // Tile size: 2^16 blocks (1 MiB) for large sequences; smaller for short ones
 // so that there are at least a few tiles per SM.
-uint32_t choose_tile_log2(uint64_t M, int num_sms)
+uint32_t tile_log2_for(uint64_t M, int num_sms)
 {
     uint32_t lg = 16;
     while (lg > 10 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
@@ -146,7 +146,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     const uint64_t a_blocks = (aad_len + 15) / 16;
     const uint64_t n_blocks = (len + 15) / 16;
     const uint64_t M = a_blocks + n_blocks;
-    const uint32_t lg = choose_tile_log2(M, ctx->num_sms);
+    const uint32_t lg = tile_log2_for(M, ctx->num_sms);
     const uint64_t K = (M + (1ull << lg) - 1) >> lg;
     uint32_t levels = 0;
     while ((1ull << levels) < K) levels++;
@@ -199,6 +199,8 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kf.n_full = len / 16;
     kf.M = M;
     kf.K = K;
+    kf.tile_begin = 0;
+    kf.tile_end = K;
     kf.tile_log2 = lg;
     kf.decrypt = decrypt ? 1u : 0u;
     kf.km = km;
@@ -261,6 +263,25 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
 {
     int rc = check_common(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, tag, mem);
     if (rc) return rc;
+    if (mem == GCM_MEM_HOST) {
+        // Host buffers are streamed through the context's chunk ring.
+        gcm_msg m;
+        m.key = key;
+        m.key_len = key_len;
+        m.iv = iv;
+        m.iv_len = iv_len;
+        m.aad = aad;
+        m.aad_len = aad_len;
+        m.in = in;
+        m.out = out;
+        m.len = len;
+        m.tag = tag;
+        int32_t st = 0;
+        rc = stream_host(ctx, &m, 1, decrypt, &st);
+        if (rc) return rc;
+        if (decrypt && st != 0) return fail(GCM_ERR_AUTH, "authentication tag mismatch: output zero-filled");
+        return GCM_OK;
+    }
     DeviceGuard guard(ctx->device);
     if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -329,6 +350,22 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
 
 }  // namespace
 
+namespace gcmgpu {
+int ctx_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int ctx_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
+uint32_t choose_tile_log2(uint64_t M, int num_sms) { return tile_log2_for(M, num_sms); }
+cudaEvent_t ctx_take_event(gcm_ctx *ctx)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    return take_event(ctx);
+}
+void ctx_record_fused(gcm_ctx *ctx, cudaEvent_t start, cudaEvent_t stop, uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->timed.push_back({start, stop, bytes});
+}
+}  // namespace gcmgpu
+
 extern "C" {
 
 const char *gcm_last_error(void) { return g_last_error.c_str(); }
@@ -370,6 +407,26 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     }
     *out = ctx;
     return GCM_OK;
+}
+
+int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (chunk_bytes < ((size_t)16 << 10) || n_buffers < 2 || n_buffers > 64)
+        return fail(GCM_ERR_INVALID_ARG, "chunk_bytes must be >= 16 KiB (whole 16 KiB tiles) and n_buffers 2..64");
+    std::lock_guard<std::mutex> lk(ctx->stream_mu);
+    ctx->chunk_bytes = chunk_bytes / ((size_t)16 << 10) * ((size_t)16 << 10);
+    ctx->n_buffers = n_buffers;
+    return GCM_OK;
+}
+
+int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t *status, int mem, void *stream)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
+    if (mem == GCM_MEM_HOST) return stream_host(ctx, msgs, n, decrypt != 0, status);
+    if (mem == GCM_MEM_DEVICE) return batch_device(ctx, msgs, n, decrypt != 0, status, static_cast<cudaStream_t>(stream));
+    return fail(GCM_ERR_INVALID_ARG, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");
 }
 
 int gcm_profile_enable(gcm_ctx *ctx, int enable)
@@ -421,6 +478,7 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
             cudaEventDestroy(t.stop);
         }
         for (auto e : ctx->spare) cudaEventDestroy(e);
+        stream_release(ctx);
         if (ctx->tabs) cudaFree(ctx->tabs);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }

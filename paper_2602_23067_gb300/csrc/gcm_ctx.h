@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "gcm_internal.h"
+#include "gcmgpu.h"
 
 struct gcm_ctx {
     int device = 0;
@@ -30,5 +31,29 @@ struct gcm_ctx {
     std::vector<cudaEvent_t> spare; // recycled events
     double fused_ms = 0.0;
     uint64_t fused_launches = 0, fused_bytes = 0;
+    // host-mode streaming (created on first use)
+    size_t chunk_bytes = (size_t)256 << 20;
+    int n_buffers = 3;
+    cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+    std::vector<cudaEvent_t> ev_h2d, ev_comp, ev_d2h;
+    std::mutex stream_mu;  // one streamed call at a time per context
+    uint8_t *ring = nullptr;        // n_buffers x chunk_bytes device chunk buffers
+    size_t ring_bytes = 0;
+    uint8_t *staging = nullptr;     // pinned host staging for tags / status words
+    size_t staging_bytes = 0;
 };
+
+namespace gcmgpu {
+// Shared between the C-ABI implementation files.
+int ctx_fail(int code, const char *msg);
+int ctx_cuda_fail(cudaError_t e, const char *where);
+uint32_t choose_tile_log2(uint64_t M, int num_sms);
+void ctx_record_fused(gcm_ctx *ctx, cudaEvent_t start, cudaEvent_t stop, uint64_t bytes);
+cudaEvent_t ctx_take_event(gcm_ctx *ctx);
+// Host-memory messages streamed through device chunk buffers (gcm_stream.cu).
+int stream_host(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status);
+void stream_release(gcm_ctx *ctx);
+// Device-memory messages in one persistent batched launch (gcm_batch.cu).
+int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status, cudaStream_t s);
+}  // namespace gcmgpu
 

@@ -18,6 +18,7 @@ constexpr int KF_LOG2_WARPS = 4;
 constexpr int GH_STRIDE = 32;
 constexpr int GH_LOG2_STRIDE = 5;
 constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
+constexpr uint32_t BATCH_TILE_LOG2 = 16;  // tile size of the batched kernel (2^16 blocks)
 constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
 
 // Shared-memory map of the fused kernel (byte offsets into dynamic smem).
@@ -36,6 +37,7 @@ struct KeyMat {
     gf128 H;                    // hash subkey E_K(0^128), poly words
     gf128 h2k[H2K_COUNT];       // H^(2^k): the stride table of the tree (Sec. 3.3.1)
     gf128 hpow[GH_STRIDE];      // H^1 .. H^32: per-lane closing factors
+    gf128 segf16[KF_WARPS];     // H^((15-w) * 2^12): warp factors for 2^16-block tiles
     uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^32, memory words
 };
 
@@ -74,12 +76,50 @@ struct KfParams {
     uint64_t n_full;        // len / 16 (whole payload blocks)
     uint64_t M;             // a_blocks + ceil(len / 16): GHASH blocks before the length block
     uint64_t K;             // number of tiles
+    uint64_t tile_begin;    // this launch processes tiles [tile_begin, tile_end)
+    uint64_t tile_end;
     uint32_t tile_log2;     // tile = 2^tile_log2 blocks, aligned to the end of the sequence
     uint32_t decrypt;
     const KeyMat *km;
     const MsgMat *mm;
     const DevTables *tabs;
     gf128 *partials;        // K tile partials, poly words
+};
+
+// One message of a device-memory batch (gcm_batch with GCM_MEM_DEVICE).
+struct BatchMsg {
+    const uint8_t *in;
+    uint8_t *out;
+    const uint8_t *aad;
+    uint64_t len;
+    uint64_t aad_len;
+    uint64_t K;             // tiles of 2^BATCH_TILE_LOG2 blocks
+    uint64_t item_base;     // index of the message's first work item
+    uint32_t nr;
+    uint32_t pad_;
+    KeyMat *km;
+    MsgMat *mm;
+    gf128 *partials;        // K entries
+    gf128 *tree;            // K/2 + 1 entries
+    uint8_t *tag;           // device: written (encrypt) or expected (decrypt)
+    int32_t *status;        // device verdict word
+};
+
+struct BatchKey {
+    uint8_t key[32];
+    uint32_t key_len;
+    uint32_t iv_len;
+    const uint8_t *iv;      // device copy of the IV
+};
+
+struct BatchParams {
+    const BatchMsg *msgs;
+    uint32_t n;
+    uint32_t decrypt;
+    uint64_t total_items;
+    unsigned long long *item_counter;  // zeroed before the launch
+    uint32_t *done;                    // n counters, zeroed before the launch
+    const DevTables *tabs;
 };
 
 struct KcParams {
@@ -108,6 +148,10 @@ cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
 cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream);
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
 cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);
+cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
+                                   const DevTables *tabs, cudaStream_t stream);
+cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t stream);
+cudaError_t launch_batch_zero(const BatchMsg *msgs, uint32_t n, cudaStream_t stream);
 cudaError_t configure_kernels();  // sets the dynamic shared memory limit
 
 }  // namespace gcmgpu

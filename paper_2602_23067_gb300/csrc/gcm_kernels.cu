@@ -104,7 +104,10 @@ __device__ int key_expand_words(const uint8_t *key, int key_len, const uint8_t *
 // ---------------------------------------------------------------------
 // KS: per-key / per-message setup (one CTA of 256 threads)
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ KsParams p)
+// The whole per-key / per-message setup, run by one CTA of 256 threads.
+// iv points to iv_len bytes (device or kernel-parameter memory).
+__device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8_t *iv, uint32_t iv_len, KeyMat *km,
+                               MsgMat *mm, const DevTables *tabs)
 {
     __shared__ uint8_t sbox[256];
     __shared__ uint32_t rkw[60];
@@ -113,12 +116,11 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
     __shared__ gf128 basis[128];
     __shared__ int s_nr;
     const int t = threadIdx.x;
-    KeyMat *km = p.km;
 
-    sbox[t] = p.tabs->sbox[t];
+    sbox[t] = tabs->sbox[t];
     __syncthreads();
     if (t == 0) {
-        int nr = key_expand_words(p.key, (int)p.key_len, sbox, rkw);
+        int nr = key_expand_words(key, (int)key_len, sbox, rkw);
         s_nr = nr;
         uint32_t zero[4] = {0u, 0u, 0u, 0u}, h[4];
         aes_block_bytes(rkw, nr, sbox, zero, h);
@@ -138,23 +140,22 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
         km->nr = (uint32_t)nr;
     } else if (t == 32) {
         // J0: IV || 0^31 || 1 for a 96-bit IV, else GHASH_H(IV || pad || [len(IV)]_64).
-        const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
         uint32_t j0[4];
-        if (p.iv_len == 12) {
+        if (iv_len == 12) {
             for (int i = 0; i < 3; i++)
                 j0[i] = (uint32_t)iv[4 * i] | ((uint32_t)iv[4 * i + 1] << 8) |
                         ((uint32_t)iv[4 * i + 2] << 16) | ((uint32_t)iv[4 * i + 3] << 24);
             j0[3] = 0x01000000u;  // bytes 12..15 = 00 00 00 01
         } else {
             gf128 y = gf_zero();
-            for (uint32_t off = 0; off < p.iv_len; off += 16) {
+            for (uint32_t off = 0; off < iv_len; off += 16) {
                 uint32_t m[4] = {0u, 0u, 0u, 0u};
-                for (uint32_t b = 0; b < 16 && off + b < p.iv_len; b++)
+                for (uint32_t b = 0; b < 16 && off + b < iv_len; b++)
                     m[b >> 2] |= (uint32_t)iv[off + b] << (8 * (b & 3));
                 y = gf_mul(gf_xor(y, gf_from_mem(m[0], m[1], m[2], m[3])), sH);
             }
             gf128 lb = gf_zero();
-            const uint64_t bits = (uint64_t)p.iv_len * 8u;
+            const uint64_t bits = (uint64_t)iv_len * 8u;
             lb.w[2] = (uint32_t)(bits >> 32);
             lb.w[3] = (uint32_t)bits;
             y = gf_mul(gf_xor(y, lb), sH);
@@ -164,8 +165,8 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
         uint32_t e[4];
         aes_block_bytes(rkw, nr, sbox, j0, e);
         for (int i = 0; i < 4; i++) {
-            p.mm->j0[i] = j0[i];
-            p.mm->ej0[i] = e[i];
+            mm->j0[i] = j0[i];
+            mm->ej0[i] = e[i];
         }
     } else if (t >= 64 && t < 64 + 60) {
         km->rk[t - 64] = (t - 64 < 4 * (nr + 1)) ? rkw[t - 64] : 0u;
@@ -192,6 +193,16 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
         }
         km->hpow[e - 1] = acc;
     }
+    if (t >= 64 && t < 64 + KF_WARPS) {
+        // H^((15-w) * 2^12) for 2^16-block tiles (the batched kernel's size).
+        const int w = t - 64, steps = KF_WARPS - 1 - w;
+        gf128 f;
+        f.w[0] = 0x80000000u;
+        f.w[1] = f.w[2] = f.w[3] = 0u;
+        for (int b = 0; b < KF_LOG2_WARPS; b++)
+            if ((steps >> b) & 1) f = gf_mul(f, sh2k[BATCH_TILE_LOG2 - KF_LOG2_WARPS + b]);
+        km->segf16[w] = f;
+    }
     __syncthreads();
     // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32.
     // Bit b of v (LSB = 0) is the coefficient of x^(8k + 7 - b).
@@ -202,6 +213,12 @@ __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ 
             if ((v >> b) & 1) acc = gf_xor(acc, basis[8 * k + 7 - b]);
         km->gtab[idx] = gf_to_mem(acc);
     }
+}
+
+__global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ KsParams p)
+{
+    const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
+    key_setup_body(p.key, p.key_len, iv, p.iv_len, p.km, p.mm, p.tabs);
 }
 
 // ---------------------------------------------------------------------
@@ -352,202 +369,449 @@ __device__ __forceinline__ uint4 keep_bytes(const uint4 &v, uint32_t nbytes)
     return make_uint4(m[0], m[1], m[2], m[3]);
 }
 
-// KF.  Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C are
-// aligned to its end (the first tile is the short one and is treated as
-// left-padded with zero blocks).  Warp w of the CTA owns segment w of the
-// tile (S = tile/16 blocks).  On whole-payload segments the warp walks
-// windows of 32 counters aligned to multiples of 32, so a window never
-// crosses a 256-counter group: rounds 1 and 2 of AES then need only the
-// lookups that depend on the counter's low byte (counter-mode caching; the
-// rest are per-group constants computed once per 256 counters).  Lane l
-// chains the l-th block of every window through acc <- acc*H^32 xor X and
-// closes the chain with H^e, e = distance of its last block from the
-// segment end; the warp's partial then moves to the tile end with
-// H^((15-w)*S).
-template <int NR>
-__global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
-{
-    extern __shared__ __align__(1024) uint8_t smem[];
-    const int tid = threadIdx.x;
-    const uint32_t lane = tid & 31;
-    const int warp = tid >> 5;
-    const uint8_t *t01 = smem + SM_T01;
-    const uint8_t *t23 = smem + SM_T23;
-    const KeyMat *km = p.km;
+// Everything a tile needs to know about its message.
+struct MsgView {
+    const uint8_t *in;
+    uint8_t *out;
+    const uint8_t *aad;
+    uint64_t len, aad_len, a_blocks, n_full, M, K;
+    uint32_t tile_log2;
+    bool dec;
+    const KeyMat *km;
+    const MsgMat *mm;
+    gf128 *partials;
+};
 
-    // Stage the replicated round tables and this key's GHASH table.
-    {
-        const uint32_t *tt = p.tabs->ttab;
-        uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
-        for (int w = tid; w < 32768; w += KF_THREADS) {
-            const int region = w >> 14, v = (w >> 6) & 255, odd = (w >> 5) & 1;
-            s32[w] = __ldg(&tt[(2 * region + odd) * 256 + v]);
-        }
-        const uint4 *g = km->gtab;
-        uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
-        for (int i = tid; i < GTAB_ENTRIES; i += KF_THREADS) sg[i] = __ldg(&g[i]);
+// Per-message constants of AES round 1: everything except the lookups of
+// counter bytes 12..15 (K0 misses byte 15, K1..K3 bytes 14, 13, 12).
+struct MsgConst {
+    uint32_t j0w0, j0w1, j0w2, ctr0, rk3, k15, K0, K1, K2, K3;
+};
+
+__device__ __forceinline__ MsgConst make_msg_const(const uint8_t *t01, const uint8_t *t23, const LaneConst &L,
+                                                   const KeyMat *km, const MsgMat *mm)
+{
+    MsgConst c;
+    c.j0w0 = __ldg(&mm->j0[0]);
+    c.j0w1 = __ldg(&mm->j0[1]);
+    c.j0w2 = __ldg(&mm->j0[2]);
+    c.ctr0 = bswap32(__ldg(&mm->j0[3]));
+    const uint32_t x0 = c.j0w0 ^ __ldg(&km->rk[0]);
+    const uint32_t x1 = c.j0w1 ^ __ldg(&km->rk[1]);
+    const uint32_t x2 = c.j0w2 ^ __ldg(&km->rk[2]);
+    c.rk3 = __ldg(&km->rk[3]);
+    c.K0 = LT0(x0, 0) ^ LT1(x1, 1) ^ LT2(x2, 2) ^ __ldg(&km->rk[4]);
+    c.K1 = LT0(x1, 0) ^ LT1(x2, 1) ^ LT3(x0, 3) ^ __ldg(&km->rk[5]);
+    c.K2 = LT0(x2, 0) ^ LT2(x0, 2) ^ LT3(x1, 3) ^ __ldg(&km->rk[6]);
+    c.K3 = LT1(x0, 1) ^ LT2(x1, 2) ^ LT3(x2, 3) ^ __ldg(&km->rk[7]);
+    c.k15 = c.rk3 >> 24;
+    return c;
+}
+
+// Stages the replicated round tables into shared memory.
+__device__ __forceinline__ void stage_round_tables(uint8_t *smem, const DevTables *tabs)
+{
+    const uint32_t *tt = tabs->ttab;
+    uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
+    for (int w = threadIdx.x; w < 32768; w += KF_THREADS) {
+        const int region = w >> 14, v = (w >> 6) & 255, odd = (w >> 5) & 1;
+        s32[w] = __ldg(&tt[(2 * region + odd) * 256 + v]);
     }
-    const uint32_t tile_log2 = p.tile_log2;
-    const int64_t seg_blocks = (int64_t)1 << (tile_log2 - KF_LOG2_WARPS);
+}
+
+__device__ __forceinline__ void stage_ghash_table(uint8_t *smem, const KeyMat *km)
+{
+    const uint4 *g = km->gtab;
+    uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
+    for (int i = threadIdx.x; i < GTAB_ENTRIES; i += KF_THREADS) sg[i] = __ldg(&g[i]);
+}
+
+// H^((15-w) * S) for every warp w, S = 2^(tile_log2 - 4): moves a warp's
+// segment partial to the tile end.  Lane 0 of each warp writes its own.
+__device__ __forceinline__ void stage_segment_factors(uint8_t *smem, const KeyMat *km, uint32_t tile_log2)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     gf128 *segf = reinterpret_cast<gf128 *>(smem + SM_SEGF);
     if (lane == 0) {
-        // H^((15-w) * S): moves warp w's segment partial to the tile end.
         gf128 f;
-        f.w[0] = 0x80000000u; f.w[1] = f.w[2] = f.w[3] = 0u;
+        f.w[0] = 0x80000000u;
+        f.w[1] = f.w[2] = f.w[3] = 0u;
         const int steps = KF_WARPS - 1 - warp;
         for (int b = 0; b < KF_LOG2_WARPS; b++)
             if ((steps >> b) & 1) f = gf_mul(f, km->h2k[tile_log2 - KF_LOG2_WARPS + b]);
         segf[warp] = f;
     }
-    uint32_t rk[4 * (NR + 1)];
-#pragma unroll
-    for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&km->rk[i]);
-    const uint32_t j0w0 = __ldg(&p.mm->j0[0]), j0w1 = __ldg(&p.mm->j0[1]), j0w2 = __ldg(&p.mm->j0[2]);
-    const uint32_t ctr0 = bswap32(__ldg(&p.mm->j0[3]));
-    const LaneConst L = make_lane_const((int)lane);
+}
+
+// Per-CTA cache of the counter-group constants of AES round 2.
+struct GroupCache {
+    uint32_t grp, G0, G1, G2, G3;
+};
+
+// One tile: Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C
+// are aligned to its end (the first tile is the short one and is treated as
+// left-padded with zero blocks).  Warp w owns segment w of the tile
+// (S = tile/16 blocks).  On whole-payload segments the warp walks windows
+// of 32 counters aligned to multiples of 32, so a window never crosses a
+// 256-counter group: rounds 1 and 2 of AES then need only the lookups that
+// depend on the counter's low byte (counter-mode caching; the rest are
+// per-group constants computed once per 256 counters).  Lane l chains the
+// l-th block of every window through acc <- acc*H^32 xor X and closes the
+// chain with H^e, e = distance of its last block from the segment end; the
+// warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
+// reduces the 16 warp partials into v.partials[tile].
+// Needs the round tables, the message's GHASH table and segment factors in
+// shared memory; contains two __syncthreads.
+template <int NR>
+__device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const MsgConst &c, const uint32_t *rk,
+                                          const LaneConst &L, uint64_t tile, GroupCache &gc)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    const KeyMat *km = v.km;
+    const gf128 *segf = reinterpret_cast<const gf128 *>(smem + SM_SEGF);
     gf128 *red = reinterpret_cast<gf128 *>(smem + SM_RED);
-    const uint64_t a_blocks = p.a_blocks;
-    const uint64_t n_full = p.n_full;
-    const bool dec = p.decrypt != 0;
-    __syncthreads();
+    const int64_t seg_blocks = (int64_t)1 << (v.tile_log2 - KF_LOG2_WARPS);
 
-    // Message constants of round 1: everything except the lookups of
-    // counter bytes 12..15 (K0 still misses byte 15, K1..K3 bytes 14, 13, 12).
-    const uint32_t x0 = j0w0 ^ __ldg(&km->rk[0]);
-    const uint32_t x1 = j0w1 ^ __ldg(&km->rk[1]);
-    const uint32_t x2 = j0w2 ^ __ldg(&km->rk[2]);
-    const uint32_t rk3 = __ldg(&km->rk[3]);
-    const uint32_t K0 = LT0(x0, 0) ^ LT1(x1, 1) ^ LT2(x2, 2) ^ __ldg(&km->rk[4]);
-    const uint32_t K1 = LT0(x1, 0) ^ LT1(x2, 1) ^ LT3(x0, 3) ^ __ldg(&km->rk[5]);
-    const uint32_t K2 = LT0(x2, 0) ^ LT2(x0, 2) ^ LT3(x1, 3) ^ __ldg(&km->rk[6]);
-    const uint32_t K3 = LT1(x0, 1) ^ LT2(x1, 2) ^ LT3(x2, 3) ^ __ldg(&km->rk[7]);
-    const uint32_t k15 = rk3 >> 24;
-    uint32_t grp = 0xFFFFFFFFu, G0 = 0, G1 = 0, G2 = 0, G3 = 0;
+    const int64_t tend = (int64_t)v.M - (int64_t)((v.K - 1 - tile) << v.tile_log2);
+    const int64_t tv_lo = tend - ((int64_t)1 << v.tile_log2);
+    const int64_t seg_hi = tv_lo + (int64_t)(warp + 1) * seg_blocks;
+    int64_t seg_lo = tv_lo + (int64_t)warp * seg_blocks;
+    if (seg_lo < 0) seg_lo = 0;
+    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t dlast = 0;
+    bool have = false;
+    uint32_t seg_len = 0;
 
-    for (uint64_t tile = blockIdx.x; tile < p.K; tile += gridDim.x) {
-        const int64_t tend = (int64_t)p.M - (int64_t)((p.K - 1 - tile) << tile_log2);
-        const int64_t tv_lo = tend - ((int64_t)1 << tile_log2);
-        const int64_t seg_hi = tv_lo + (int64_t)(warp + 1) * seg_blocks;
-        int64_t seg_lo = tv_lo + (int64_t)warp * seg_blocks;
-        if (seg_lo < 0) seg_lo = 0;
-        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
-        uint32_t dlast = 0;
-        bool have = false;
-        uint32_t seg_len = 0;
-
-        if (seg_hi > seg_lo) {
-            seg_len = (uint32_t)(seg_hi - seg_lo);
-            if ((uint64_t)seg_lo >= a_blocks && (uint64_t)seg_hi <= a_blocks + n_full) {
-                // Whole payload blocks: counter-aligned windows of 32.
-                const uint64_t j_lo = (uint64_t)seg_lo - a_blocks;
-                const uint32_t c_lo = ctr0 + 1u + (uint32_t)j_lo;
-                const uint32_t W0 = c_lo & ~31u;
-                const uint32_t nwin = (seg_len + (c_lo & 31u) + 31u) >> 5;
-                const uint4 *in = reinterpret_cast<const uint4 *>(p.in) + j_lo;
-                uint4 *out = reinterpret_cast<uint4 *>(p.out) + j_lo;
-                for (uint32_t wi = 0; wi < nwin; wi++) {
-                    const uint32_t W = W0 + (wi << 5);
-                    const uint32_t d = W + lane - c_lo;
-                    const bool active = d < seg_len;
-                    uint4 din = make_uint4(0u, 0u, 0u, 0u);
-                    if (active) din = __ldcs(in + d);
-                    if ((W >> 8) != grp) {
-                        // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
-                        grp = W >> 8;
-                        const uint32_t x3g = bswap32(W) ^ rk3;
-                        const uint32_t u1 = K1 ^ LT2(x3g, 2);
-                        const uint32_t u2 = K2 ^ LT1(x3g, 1);
-                        const uint32_t u3 = K3 ^ LT0(x3g, 0);
-                        G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
-                        G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
-                        G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
-                        G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
-                    }
-                    // Round 1 column 0 (the only column that sees counter byte 15),
-                    // then round 2 (one varying lookup per column).
-                    const uint32_t x15 = ((W & 0xE0u) | lane) ^ k15;
-                    const uint32_t v0 = K0 ^ LT3(x15, 0);
-                    uint4 ks = aes_rounds_from3<NR>(t01, t23, L, G0 ^ LT0(v0, 0), G1 ^ LT3(v0, 3),
-                                                    G2 ^ LT2(v0, 2), G3 ^ LT1(v0, 1), rk);
-                    if (active) {
-                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                        __stcs(out + d, ks);
-                        uint4 m = ghash_mul_table(smem, acc, L);
-                        xor4(m, dec ? din : ks);
-                        acc = m;
-                        dlast = d;
-                        have = true;
-                    }
+    if (seg_hi > seg_lo) {
+        seg_len = (uint32_t)(seg_hi - seg_lo);
+        if ((uint64_t)seg_lo >= v.a_blocks && (uint64_t)seg_hi <= v.a_blocks + v.n_full) {
+            // Whole payload blocks: counter-aligned windows of 32.
+            const uint64_t j_lo = (uint64_t)seg_lo - v.a_blocks;
+            const uint32_t c_lo = c.ctr0 + 1u + (uint32_t)j_lo;
+            const uint32_t W0 = c_lo & ~31u;
+            const uint32_t nwin = (seg_len + (c_lo & 31u) + 31u) >> 5;
+            const uint4 *in = reinterpret_cast<const uint4 *>(v.in) + j_lo;
+            uint4 *out = reinterpret_cast<uint4 *>(v.out) + j_lo;
+            for (uint32_t wi = 0; wi < nwin; wi++) {
+                const uint32_t W = W0 + (wi << 5);
+                const uint32_t d = W + lane - c_lo;
+                const bool active = d < seg_len;
+                uint4 din = make_uint4(0u, 0u, 0u, 0u);
+                if (active) din = __ldcs(in + d);
+                if ((W >> 8) != gc.grp) {
+                    // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
+                    gc.grp = W >> 8;
+                    const uint32_t x3g = bswap32(W) ^ c.rk3;
+                    const uint32_t u1 = c.K1 ^ LT2(x3g, 2);
+                    const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
+                    const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
+                    gc.G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
+                    gc.G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
+                    gc.G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
+                    gc.G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
                 }
-            } else {
-                // Segments that touch the AAD or the final partial block.
-                uint32_t rlo[12];
-#pragma unroll
-                for (int i = 0; i < 12; i++) rlo[i] = __ldg(&km->rk[i]);
-                for (uint32_t q = lane; q < seg_len; q += 32) {
-                    const uint64_t s = (uint64_t)seg_lo + q;
-                    uint4 x;
-                    if (s < a_blocks) {
-                        const uint64_t off = s * 16u;
-                        const uint64_t rem = p.aad_len - off;
-                        const uint8_t *src = p.aad + off;
-                        if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
-                            x = *reinterpret_cast<const uint4 *>(src);
-                        else
-                            x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
-                    } else {
-                        const uint64_t j = s - a_blocks;
-                        const uint32_t ctr = ctr0 + 1u + (uint32_t)j;
-                        uint32_t s0 = j0w0 ^ rlo[0], s1 = j0w1 ^ rlo[1], s2 = j0w2 ^ rlo[2];
-                        uint32_t s3 = bswap32(ctr) ^ rlo[3];
-                        aes_round(t01, t23, L, s0, s1, s2, s3, rlo[4], rlo[5], rlo[6], rlo[7]);
-                        aes_round(t01, t23, L, s0, s1, s2, s3, rlo[8], rlo[9], rlo[10], rlo[11]);
-                        uint4 ks = aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
-                        if (j < n_full) {
-                            const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(p.in) + j);
-                            ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                            __stcs(reinterpret_cast<uint4 *>(p.out) + j, ks);
-                            x = dec ? din : ks;
-                        } else {
-                            const uint32_t nb = (uint32_t)(p.len - j * 16u);
-                            const uint4 din = load_partial(p.in + j * 16u, nb);
-                            ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                            const uint4 c = keep_bytes(ks, nb);
-                            store_partial(p.out + j * 16u, c, nb);
-                            x = dec ? din : c;
-                        }
-                    }
+                // Round 1 column 0 (the only column that sees counter byte 15),
+                // then round 2 (one varying lookup per column).
+                const uint32_t x15 = ((W & 0xE0u) | lane) ^ c.k15;
+                const uint32_t v0 = c.K0 ^ LT3(x15, 0);
+                uint4 ks = aes_rounds_from3<NR>(t01, t23, L, gc.G0 ^ LT0(v0, 0), gc.G1 ^ LT3(v0, 3),
+                                                gc.G2 ^ LT2(v0, 2), gc.G3 ^ LT1(v0, 1), rk);
+                if (active) {
+                    ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                    __stcs(out + d, ks);
                     uint4 m = ghash_mul_table(smem, acc, L);
-                    xor4(m, x);
+                    xor4(m, v.dec ? din : ks);
                     acc = m;
-                    dlast = q;
+                    dlast = d;
                     have = true;
                 }
             }
+        } else {
+            // Segments that touch the AAD or the final partial block.
+            uint32_t rlo[12];
+#pragma unroll
+            for (int i = 0; i < 12; i++) rlo[i] = __ldg(&km->rk[i]);
+            for (uint32_t q = lane; q < seg_len; q += 32) {
+                const uint64_t s = (uint64_t)seg_lo + q;
+                uint4 x;
+                if (s < v.a_blocks) {
+                    const uint64_t off = s * 16u;
+                    const uint64_t rem = v.aad_len - off;
+                    const uint8_t *src = v.aad + off;
+                    if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
+                        x = *reinterpret_cast<const uint4 *>(src);
+                    else
+                        x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
+                } else {
+                    const uint64_t j = s - v.a_blocks;
+                    const uint32_t ctr = c.ctr0 + 1u + (uint32_t)j;
+                    uint32_t s0 = c.j0w0 ^ rlo[0], s1 = c.j0w1 ^ rlo[1], s2 = c.j0w2 ^ rlo[2];
+                    uint32_t s3 = bswap32(ctr) ^ rlo[3];
+                    aes_round(t01, t23, L, s0, s1, s2, s3, rlo[4], rlo[5], rlo[6], rlo[7]);
+                    aes_round(t01, t23, L, s0, s1, s2, s3, rlo[8], rlo[9], rlo[10], rlo[11]);
+                    uint4 ks = aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
+                    if (j < v.n_full) {
+                        const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(v.in) + j);
+                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                        __stcs(reinterpret_cast<uint4 *>(v.out) + j, ks);
+                        x = v.dec ? din : ks;
+                    } else {
+                        const uint32_t nb = (uint32_t)(v.len - j * 16u);
+                        const uint4 din = load_partial(v.in + j * 16u, nb);
+                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                        const uint4 cb = keep_bytes(ks, nb);
+                        store_partial(v.out + j * 16u, cb, nb);
+                        x = v.dec ? din : cb;
+                    }
+                }
+                uint4 m = ghash_mul_table(smem, acc, L);
+                xor4(m, x);
+                acc = m;
+                dlast = q;
+                have = true;
+            }
         }
+    }
 
-        // Close the lane's chain (its last block is e = seg_len - dlast blocks
-        // before the segment end, 1 <= e <= 32), reduce the warp, move the
-        // warp's partial to the tile end, reduce the CTA.
-        gf128 z = gf_zero();
-        if (have) z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), km->hpow[seg_len - dlast - 1]);
+    // Close the lane's chain (its last block is e = seg_len - dlast blocks
+    // before the segment end, 1 <= e <= 32), reduce the warp, move the
+    // warp's partial to the tile end, reduce the CTA.
+    gf128 z = gf_zero();
+    if (have) z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), km->hpow[seg_len - dlast - 1]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
+    if (lane == 0) red[warp] = (warp == KF_WARPS - 1) ? z : gf_mul(z, segf[warp]);
+    __syncthreads();
+    if (warp == 0) {
+        z = (lane < KF_WARPS) ? red[lane] : gf_zero();
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
             for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
-        if (lane == 0) red[warp] = (warp == KF_WARPS - 1) ? z : gf_mul(z, segf[warp]);
-        __syncthreads();
-        if (warp == 0) {
-            z = (lane < KF_WARPS) ? red[lane] : gf_zero();
+        if (lane == 0) v.partials[tile] = z;
+    }
+    __syncthreads();
+}
+
+// KF: one message, tiles [tile_begin, tile_end) over a persistent grid.
+template <int NR>
+__global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    stage_round_tables(smem, p.tabs);
+    stage_ghash_table(smem, p.km);
+    stage_segment_factors(smem, p.km, p.tile_log2);
+    uint32_t rk[4 * (NR + 1)];
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
+    for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&p.km->rk[i]);
+    const LaneConst L = make_lane_const((int)(threadIdx.x & 31));
+    MsgView v;
+    v.in = p.in;
+    v.out = p.out;
+    v.aad = p.aad;
+    v.len = p.len;
+    v.aad_len = p.aad_len;
+    v.a_blocks = p.a_blocks;
+    v.n_full = p.n_full;
+    v.M = p.M;
+    v.K = p.K;
+    v.tile_log2 = p.tile_log2;
+    v.dec = p.decrypt != 0;
+    v.km = p.km;
+    v.mm = p.mm;
+    v.partials = p.partials;
+    __syncthreads();
+    const MsgConst c = make_msg_const(t01, t23, L, p.km, p.mm);
+    GroupCache gc;
+    gc.grp = 0xFFFFFFFFu;
+    gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
+    for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
+        tile_body<NR>(smem, v, c, rk, L, tile, gc);
+}
+
+// ---------------------------------------------------------------------
+// KB: many messages in one persistent launch
+// ---------------------------------------------------------------------
+template <int NR>
+__device__ __noinline__ void batch_tile(uint8_t *smem, const MsgView &v, const LaneConst &L, uint64_t tile,
+                                        GroupCache &gc)
+{
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    uint32_t rk[4 * (NR + 1)];
 #pragma unroll
-                for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
-            if (lane == 0) p.partials[tile] = z;
+    for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&v.km->rk[i]);
+    const MsgConst c = make_msg_const(t01, t23, L, v.km, v.mm);
+    tile_body<NR>(smem, v, c, rk, L, tile, gc);
+}
+
+// The CTA that finishes a message's last tile combines its partials (the
+// same right-to-left tree as combine_kernel, inside one CTA) and writes the
+// tag, or the verdict for decryption.
+__device__ void batch_combine(const BatchMsg &m, bool dec)
+{
+    const int t = threadIdx.x;
+    uint64_t cnt = m.K;
+    int level = 0;
+    gf128 *src = m.partials;
+    gf128 *dst = m.tree;
+    bool reversed = true;
+    while (cnt > 1) {
+        const uint64_t half = (cnt + 1) / 2;
+        const gf128 mult = m.km->h2k[BATCH_TILE_LOG2 + level];
+        for (uint64_t g = t; g < half; g += blockDim.x) {
+            const uint64_t ri = 2 * g, li = 2 * g + 1;
+            gf128 right, left;
+            const gf128 *pr = reversed ? &src[cnt - 1 - ri] : &src[ri];
+            for (int k = 0; k < 4; k++) right.w[k] = __ldcg(&pr->w[k]);
+            gf128 val = right;
+            if (li < cnt) {
+                const gf128 *pl = reversed ? &src[cnt - 1 - li] : &src[li];
+                for (int k = 0; k < 4; k++) left.w[k] = __ldcg(&pl->w[k]);
+                val = gf_xor(gf_mul(left, mult), right);
+            }
+            for (int k = 0; k < 4; k++) __stcg(&dst[g].w[k], val.w[k]);
         }
+        __threadfence_block();
         __syncthreads();
+        gf128 *tmp = src;
+        src = dst;
+        dst = tmp;
+        reversed = false;
+        cnt = half;
+        level++;
+    }
+    if (t == 0) {
+        gf128 s = gf_zero();
+        if (cnt == 1)
+            for (int k = 0; k < 4; k++) s.w[k] = __ldcg(&src[0].w[k]);
+        gf128 lb;
+        const uint64_t abits = m.aad_len * 8u, cbits = m.len * 8u;
+        lb.w[0] = (uint32_t)(abits >> 32);
+        lb.w[1] = (uint32_t)abits;
+        lb.w[2] = (uint32_t)(cbits >> 32);
+        lb.w[3] = (uint32_t)cbits;
+        const gf128 gh = gf_mul(gf_xor(s, lb), m.km->H);
+        const uint4 gm = gf_to_mem(gh);
+        const uint32_t tw[4] = {gm.x ^ m.mm->ej0[0], gm.y ^ m.mm->ej0[1], gm.z ^ m.mm->ej0[2], gm.w ^ m.mm->ej0[3]};
+        uint32_t diff = 0;
+        for (int b = 0; b < 16; b++) {
+            const uint8_t tb = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
+            if (dec)
+                diff |= (uint32_t)(tb ^ m.tag[b]);
+            else
+                m.tag[b] = tb;
+        }
+        *m.status = dec ? (diff ? -3 : 0) : 0;
     }
 }
+
+__global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_constant__ BatchParams p)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ uint64_t s_item;
+    __shared__ uint32_t s_msg;
+    __shared__ int s_last;
+    stage_round_tables(smem, p.tabs);
+    const LaneConst L = make_lane_const((int)(threadIdx.x & 31));
+    uint32_t cur = 0xFFFFFFFFu;
+    GroupCache gc;
+    for (;;) {
+        __syncthreads();  // previous item (and its tables) fully done
+        if (threadIdx.x == 0) {
+            const uint64_t item = atomicAdd(p.item_counter, 1ull);
+            s_item = item;
+            if (item < p.total_items) {
+                // The message whose item range holds `item` (item_base is sorted).
+                uint32_t lo = 0, hi = p.n - 1;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) / 2;
+                    if (p.msgs[mid].item_base <= item) lo = mid;
+                    else hi = mid - 1;
+                }
+                s_msg = lo;
+            }
+        }
+        __syncthreads();
+        const uint64_t item = s_item;
+        if (item >= p.total_items) break;
+        const uint32_t mi = s_msg;
+        const BatchMsg &bm = p.msgs[mi];
+        MsgView v;
+        v.in = bm.in;
+        v.out = bm.out;
+        v.aad = bm.aad;
+        v.len = bm.len;
+        v.aad_len = bm.aad_len;
+        v.a_blocks = (bm.aad_len + 15) / 16;
+        v.n_full = bm.len / 16;
+        v.M = v.a_blocks + (bm.len + 15) / 16;
+        v.K = bm.K;
+        v.tile_log2 = BATCH_TILE_LOG2;
+        v.dec = p.decrypt != 0;
+        v.km = bm.km;
+        v.mm = bm.mm;
+        v.partials = bm.partials;
+        if (mi != cur) {
+            // New key: its GHASH table and segment factors.
+            stage_ghash_table(smem, bm.km);
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            if (lane == 0) reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf16[warp];
+            cur = mi;
+            gc.grp = 0xFFFFFFFFu;
+            __syncthreads();
+        }
+        const uint64_t tile = item - bm.item_base;
+        if (bm.nr == 14)
+            batch_tile<14>(smem, v, L, tile, gc);
+        else if (bm.nr == 10)
+            batch_tile<10>(smem, v, L, tile, gc);
+        else
+            batch_tile<12>(smem, v, L, tile, gc);
+        // tile_body ended with __syncthreads after warp 0 lane 0 stored the
+        // partial; publish it and count the message's finished tiles.
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const uint32_t prev = atomicAdd(&p.done[mi], 1u);
+            s_last = (prev + 1 == (uint32_t)bm.K) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            batch_combine(bm, p.decrypt != 0);
+        }
+    }
+}
+
+// Zero-fills the outputs of messages whose tag failed (one CTA per message).
+__global__ void __launch_bounds__(256) batch_zero_kernel(const BatchMsg *msgs, uint32_t n)
+{
+    const uint32_t mi = blockIdx.x;
+    if (mi >= n) return;
+    const BatchMsg &m = msgs[mi];
+    if (*m.status == 0) return;
+    const uint64_t nvec = m.len / 16;
+    uint4 *o = reinterpret_cast<uint4 *>(m.out);
+    for (uint64_t i = threadIdx.x; i < nvec; i += blockDim.x) o[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (threadIdx.x < (m.len & 15)) m.out[nvec * 16 + threadIdx.x] = 0;
+}
+
+// Key setup for many messages: one CTA each.
+__global__ void __launch_bounds__(256) batch_key_setup_kernel(const BatchMsg *msgs, const BatchKey *keys,
+                                                              const DevTables *tabs)
+{
+    const BatchMsg &m = msgs[blockIdx.x];
+    const BatchKey &k = keys[blockIdx.x];
+    key_setup_body(k.key, k.key_len, k.iv, k.iv_len, m.km, m.mm, tabs);
+}
+
 #undef LT0
 #undef LT1
 #undef LT2
@@ -633,9 +897,33 @@ __global__ void __launch_bounds__(256) zero_on_fail_kernel(const __grid_constant
 // ---------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------
+cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
+                                   const DevTables *tabs, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    batch_key_setup_kernel<<<n, 256, 0, stream>>>(msgs, keys, tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t stream)
+{
+    if (p.total_items == 0) return cudaSuccess;
+    batch_kernel<<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_zero(const BatchMsg *msgs, uint32_t n, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    batch_zero_kernel<<<n, 256, 0, stream>>>(msgs, n);
+    return cudaGetLastError();
+}
+
 cudaError_t configure_kernels()
 {
     cudaError_t e;
+    e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fused_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(fused_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
@@ -657,7 +945,7 @@ cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream)
 
 cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream)
 {
-    if (p.K == 0) return cudaSuccess;
+    if (p.tile_end <= p.tile_begin) return cudaSuccess;
     switch (nr) {
     case 10: fused_kernel<10><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
     case 12: fused_kernel<12><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;

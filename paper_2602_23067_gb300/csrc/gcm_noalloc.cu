@@ -175,6 +175,8 @@ extern "C" int gcm_encrypt_noalloc(const uint8_t *key, size_t key_len, const uin
     kf.n_full = len / 16;
     kf.M = M;
     kf.K = K;
+    kf.tile_begin = 0;
+    kf.tile_end = K;
     kf.tile_log2 = lg;
     kf.decrypt = 0;
     kf.km = km;
