@@ -151,6 +151,13 @@ typedef struct {
 int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
               int32_t *status, int mem, void *stream);
 
+/* gcm_batch in device memory that also reports, per message, the device
+ * time (ns, from the GPU's global timer) between the start of the batch's
+ * key setup and the completion of that message's tag (done_ns: host array
+ * of n).  Used to measure per-message latency inside one persistent launch. */
+int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
+                    int32_t *status, uint64_t *done_ns, void *stream);
+
 /* Host-mode streaming geometry: chunk_bytes of payload per chunk (rounded
  * to whole tiles) and n_buffers device chunk buffers in the ring (>= 2).
  * Defaults: 256 MiB and 3. */

@@ -79,6 +79,8 @@ SIGNATURES = {
     "gcm_batch": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int, _VP]),
     "gcm_ctx_set_streaming": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
+    "gcm_batch_timed": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_uint64), _VP]),
     "gfc_fits_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP,
                                         ctypes.POINTER(GfcResult)]),
     "gfc_fits_decrypt_verify": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, ctypes.c_int,

@@ -425,8 +425,17 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t 
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
     if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
     if (mem == GCM_MEM_HOST) return stream_host(ctx, msgs, n, decrypt != 0, status);
-    if (mem == GCM_MEM_DEVICE) return batch_device(ctx, msgs, n, decrypt != 0, status, static_cast<cudaStream_t>(stream));
+    if (mem == GCM_MEM_DEVICE)
+        return batch_device(ctx, msgs, n, decrypt != 0, status, nullptr, static_cast<cudaStream_t>(stream));
     return fail(GCM_ERR_INVALID_ARG, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");
+}
+
+int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t *status, uint64_t *done_ns,
+                    void *stream)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
+    return batch_device(ctx, msgs, n, decrypt != 0, status, done_ns, static_cast<cudaStream_t>(stream));
 }
 
 int gcm_profile_enable(gcm_ctx *ctx, int enable)

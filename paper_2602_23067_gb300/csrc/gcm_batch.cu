@@ -43,7 +43,8 @@ int check_device_msg(const gcm_msg &m)
 
 }  // namespace
 
-int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status, cudaStream_t s)
+int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status, uint64_t *done_ns,
+                 cudaStream_t s)
 {
     for (size_t i = 0; i < n; i++) {
         int rc = check_device_msg(msgs[i]);
@@ -94,6 +95,8 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     const size_t o_status = off;
     off = al(off + n * sizeof(int32_t));
     const size_t counters_bytes = off - o_done;
+    const size_t o_times = off;  // t_start, then one completion time per message
+    off = al(off + (n + 1) * sizeof(uint64_t));
     for (size_t i = 0; i < n; i++) {
         o_km[i] = off;
         off = al(off + sizeof(KeyMat) + sizeof(MsgMat));
@@ -107,7 +110,7 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
         return ctx_fail(GCM_ERR_NO_MEMORY, "batch scratch would exceed the context's HBM budget");
 
     // Pinned staging for the descriptors and for the verdicts coming back.
-    const size_t stage_need = al(host_bytes) + al(n * sizeof(int32_t));
+    const size_t stage_need = al(host_bytes) + al(n * sizeof(int32_t)) + al((n + 1) * sizeof(uint64_t));
     if (ctx->staging_bytes < stage_need) {
         if (ctx->staging) cudaFreeHost(ctx->staging);
         ctx->staging = nullptr;
@@ -146,6 +149,7 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
         b.tree = reinterpret_cast<gf128 *>(dev + o_tree[i]);
         b.tag = m.tag;
         b.status = reinterpret_cast<int32_t *>(dev + o_status) + i;
+        b.t_done = done_ns ? reinterpret_cast<uint64_t *>(dev + o_times) + 1 + i : nullptr;
         BatchKey &k = hk[i];
         memset(&k, 0, sizeof(k));
         memcpy(k.key, m.key, m.key_len);
@@ -158,7 +162,8 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     if (e == cudaSuccess) e = cudaMemsetAsync(dev + o_done, 0, counters_bytes, s);
     if (e == cudaSuccess)
         e = launch_batch_key_setup(reinterpret_cast<const BatchMsg *>(dev + o_msgs),
-                                   reinterpret_cast<const BatchKey *>(dev + o_keys), (uint32_t)n, ctx->tabs, s);
+                                   reinterpret_cast<const BatchKey *>(dev + o_keys), (uint32_t)n, ctx->tabs,
+                                   done_ns ? reinterpret_cast<uint64_t *>(dev + o_times) : nullptr, s);
     ctx->launches += 1;
     BatchParams bp;
     memset(&bp, 0, sizeof(bp));
@@ -189,13 +194,18 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
         ctx->launches += 1;
     }
     int32_t *hstat = reinterpret_cast<int32_t *>(stage + al(host_bytes));
+    uint64_t *htimes = reinterpret_cast<uint64_t *>(stage + al(host_bytes) + al(n * sizeof(int32_t)));
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(hstat, dev + o_status, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && done_ns)
+        e = cudaMemcpyAsync(htimes, dev + o_times, (n + 1) * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaFreeAsync(dev, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "batched launch");
     if (status)
         for (size_t i = 0; i < n; i++) status[i] = hstat[i] ? GCM_ERR_AUTH : 0;
+    if (done_ns)
+        for (size_t i = 0; i < n; i++) done_ns[i] = htimes[1 + i] - htimes[0];
     return GCM_OK;
 }
 

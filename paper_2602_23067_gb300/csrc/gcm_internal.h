@@ -103,6 +103,7 @@ struct BatchMsg {
     gf128 *tree;            // K/2 + 1 entries
     uint8_t *tag;           // device: written (encrypt) or expected (decrypt)
     int32_t *status;        // device verdict word
+    uint64_t *t_done;       // device: %globaltimer when the message completed (or null)
 };
 
 struct BatchKey {
@@ -149,7 +150,7 @@ cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t strea
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
 cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
-                                   const DevTables *tabs, cudaStream_t stream);
+                                   const DevTables *tabs, uint64_t *t_start, cudaStream_t stream);
 cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_batch_zero(const BatchMsg *msgs, uint32_t n, cudaStream_t stream);
 cudaError_t configure_kernels();  // sets the dynamic shared memory limit

@@ -710,6 +710,11 @@ __device__ void batch_combine(const BatchMsg &m, bool dec)
                 m.tag[b] = tb;
         }
         *m.status = dec ? (diff ? -3 : 0) : 0;
+        if (m.t_done) {
+            uint64_t now;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+            *m.t_done = now;
+        }
     }
 }
 
@@ -805,8 +810,13 @@ __global__ void __launch_bounds__(256) batch_zero_kernel(const BatchMsg *msgs, u
 
 // Key setup for many messages: one CTA each.
 __global__ void __launch_bounds__(256) batch_key_setup_kernel(const BatchMsg *msgs, const BatchKey *keys,
-                                                              const DevTables *tabs)
+                                                              const DevTables *tabs, uint64_t *t_start)
 {
+    if (t_start && blockIdx.x == 0 && threadIdx.x == 0) {
+        uint64_t now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        *t_start = now;
+    }
     const BatchMsg &m = msgs[blockIdx.x];
     const BatchKey &k = keys[blockIdx.x];
     key_setup_body(k.key, k.key_len, k.iv, k.iv_len, m.km, m.mm, tabs);
@@ -898,10 +908,10 @@ __global__ void __launch_bounds__(256) zero_on_fail_kernel(const __grid_constant
 // Launchers
 // ---------------------------------------------------------------------
 cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
-                                   const DevTables *tabs, cudaStream_t stream)
+                                   const DevTables *tabs, uint64_t *t_start, cudaStream_t stream)
 {
     if (n == 0) return cudaSuccess;
-    batch_key_setup_kernel<<<n, 256, 0, stream>>>(msgs, keys, tabs);
+    batch_key_setup_kernel<<<n, 256, 0, stream>>>(msgs, keys, tabs, t_start);
     return cudaGetLastError();
 }
 
