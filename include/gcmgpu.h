@@ -164,6 +164,72 @@ int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
 int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers);
 
 /* ---------------------------------------------------------------- */
+/* Key cache and the continuous-batching server                     */
+/* ---------------------------------------------------------------- */
+
+/* Builds a key's material once on the device (round keys, H, powers of H,
+ * the GHASH table: about 74 KiB) and returns a handle for server requests.
+ * Register keys before submitting requests that use them. */
+int gcm_key_register(gcm_ctx *ctx, const uint8_t *key, size_t key_len, uint32_t *handle);
+
+typedef struct gcm_server gcm_server;
+
+/* One request.  All pointers are host pointers; in/out/aad/tag must stay
+ * valid until the request completes (pinned memory lets the copies run
+ * asynchronously).  tag receives the tag (op 0) or holds the expected tag
+ * (op 1, read at submit).  arrival_ns (the library clock, gcm_now_ns) is the
+ * arrival time used for latency; 0 means "now". */
+typedef struct {
+    int op;                 /* 0 = encrypt, 1 = decrypt-verify */
+    uint32_t key;           /* handle from gcm_key_register */
+    const uint8_t *iv;
+    size_t iv_len;
+    const uint8_t *aad;
+    size_t aad_len;
+    const uint8_t *in;
+    uint8_t *out;
+    size_t len;
+    uint8_t *tag;
+    uint64_t arrival_ns;
+    uint64_t user;          /* copied to the completion */
+} gcm_request;
+
+typedef struct {
+    uint64_t ticket;
+    int32_t status;         /* 0, GCM_ERR_AUTH (output zero-filled) or an error */
+    uint64_t arrival_ns;
+    uint64_t complete_ns;   /* library clock when the outputs were in host memory */
+    uint64_t user;
+} gcm_completion;
+
+/* Starts a server thread on the context's device.  hbm_budget_bytes bounds
+ * the device memory of all waves in flight (0 = 40 GB); max_wave_msgs bounds
+ * the requests per wave; max_inflight (1..8) waves may be in flight at once.
+ * max_wave_msgs = max_inflight = 1 gives a one-request-per-launch server. */
+int gcm_server_create(gcm_ctx *ctx, size_t hbm_budget_bytes, size_t max_wave_msgs, int max_inflight,
+                      gcm_server **out);
+
+/* Queues a request (thread-safe, does not block on the GPU).  Returns
+ * GCM_ERR_BUSY when the queue is full, GCM_ERR_NO_MEMORY when the request
+ * alone exceeds the HBM budget. */
+int gcm_server_submit(gcm_server *srv, const gcm_request *req, uint64_t *ticket);
+
+/* Moves up to max completions into out; returns how many. */
+size_t gcm_server_poll(gcm_server *srv, gcm_completion *out, size_t max);
+
+/* Counters: waves launched, requests launched, requests queued, device
+ * bytes held by waves in flight.  Returns 0, or the error that stopped the
+ * server. */
+int gcm_server_stats(gcm_server *srv, uint64_t *waves, uint64_t *messages, size_t *queued,
+                     size_t *bytes_in_flight);
+
+/* Finishes the queued requests, stops the thread, frees the server. */
+void gcm_server_destroy(gcm_server *srv);
+
+/* The library's monotonic clock in nanoseconds (for arrival_ns). */
+uint64_t gcm_now_ns(void);
+
+/* ---------------------------------------------------------------- */
 /* Measurement hooks (used by the benchmark; no counterpart in the  */
 /* paper beyond its cudaEventRecord protocol, Sec. 5.3.1)           */
 /* ---------------------------------------------------------------- */

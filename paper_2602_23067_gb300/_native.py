@@ -61,6 +61,18 @@ class GcmMsg(ctypes.Structure):
                 ("tag", ctypes.c_void_p)]
 
 
+class GcmRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int), ("key", ctypes.c_uint32), ("iv", ctypes.c_void_p), ("iv_len", ctypes.c_size_t),
+                ("aad", ctypes.c_void_p), ("aad_len", ctypes.c_size_t), ("in_", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("len", ctypes.c_size_t), ("tag", ctypes.c_void_p),
+                ("arrival_ns", ctypes.c_uint64), ("user", ctypes.c_uint64)]
+
+
+class GcmCompletion(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int32), ("arrival_ns", ctypes.c_uint64),
+                ("complete_ns", ctypes.c_uint64), ("user", ctypes.c_uint64)]
+
+
 # Every symbol the header declares, with its ctypes signature.
 _VP = ctypes.c_void_p
 _SZ = ctypes.c_size_t
@@ -79,6 +91,14 @@ SIGNATURES = {
     "gcm_batch": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int, _VP]),
     "gcm_ctx_set_streaming": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
+    "gcm_key_register": (ctypes.c_int, [_VP, _VP, _SZ, ctypes.POINTER(ctypes.c_uint32)]),
+    "gcm_server_create": (ctypes.c_int, [_VP, _SZ, _SZ, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "gcm_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(GcmRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "gcm_server_poll": (ctypes.c_size_t, [_VP, ctypes.POINTER(GcmCompletion), _SZ]),
+    "gcm_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "gcm_server_destroy": (None, [_VP]),
+    "gcm_now_ns": (ctypes.c_uint64, []),
     "gcm_batch_timed": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_uint64), _VP]),
     "gfc_fits_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP, ctypes.c_int, ctypes.c_int, _VP,

@@ -17,7 +17,7 @@ from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GFC_AA
 __all__ = [
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
     "gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "last_error",
-    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL",
+    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server",
 ]
 
 
@@ -220,6 +220,17 @@ class Context:
         check(lib.gcm_batch(self.handle, arr, n, 1 if decrypt else 0, status, mem, st))
         return [int(status[i]) for i in range(n)]
 
+    # -- key cache and serving ----------------------------------------------
+    def key_register(self, key: bytes) -> int:
+        """gcm_key_register: builds the key's material once on the device."""
+        kp, kl, kk = _host_buf(key)
+        h = ctypes.c_uint32()
+        check(lib.gcm_key_register(self.handle, kp, kl, ctypes.byref(h)))
+        return h.value
+
+    def server(self, hbm_budget_bytes: int = 0, max_wave_msgs: int = 4096, max_inflight: int = 3) -> "Server":
+        return Server(self, hbm_budget_bytes, max_wave_msgs, max_inflight)
+
     # -- FITS files (header in clear, data unit encrypted) ------------------
     def _fits_common(self, decrypt, key, fits, iv, tag, aad_mode, stream):
         import numpy as np
@@ -337,3 +348,61 @@ def _dev_tensor_copy(ptr: int, n: int, device):
     out = view.clone()
     torch.cuda.synchronize(device)
     return out
+
+
+class Server:
+    """The continuous-batching server (gcm_server_*).  Requests reference host
+    buffers that must stay alive until their completion is polled."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int, max_wave_msgs: int, max_inflight: int):
+        from ._native import GcmCompletion
+
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        check(lib.gcm_server_create(ctx.handle, hbm_budget_bytes, max_wave_msgs, max_inflight, ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+        self._buf = (GcmCompletion * 4096)()
+
+    def submit(self, op: int, key_handle: int, iv: bytes, aad, inp, out, tag, arrival_ns: int = 0,
+               user: int = 0) -> int:
+        """Queues a request on host buffers (bytes/numpy/pinned tensors); the
+        tag buffer receives the tag (op 0) or holds the expected tag (op 1)."""
+        from ._native import GcmRequest
+
+        ivp, ivl, ivk = _host_buf(iv)
+        ap, al, ak = _host_buf(aad)
+        pp, pl, pk = _host_buf(inp)
+        op_, ol, ok = _host_buf(out)
+        tp, tl, tk = _host_buf(tag)
+        req = GcmRequest(op, key_handle, ivp, ivl, ap or None, al, pp or None, op_ or None, pl, tp, arrival_ns, user)
+        t = ctypes.c_uint64()
+        check(lib.gcm_server_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (ivk, ak, pk, ok, tk)
+        return t.value
+
+    def poll(self):
+        """Returns a list of (ticket, status, arrival_ns, complete_ns, user)."""
+        n = lib.gcm_server_poll(self.handle, self._buf, len(self._buf))
+        out = []
+        for i in range(n):
+            c = self._buf[i]
+            self._keep.pop(c.ticket, None)
+            out.append((c.ticket, c.status, c.arrival_ns, c.complete_ns, c.user))
+        return out
+
+    def stats(self):
+        w, m, q, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_size_t()
+        rc = lib.gcm_server_stats(self.handle, ctypes.byref(w), ctypes.byref(m), ctypes.byref(q), ctypes.byref(b))
+        return {"waves": w.value, "messages": m.value, "queued": q.value, "bytes_in_flight": b.value, "error": rc}
+
+    def close(self) -> None:
+        if self.handle:
+            lib.gcm_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libgcmgpu.so")
 BUILD_DIR = os.path.join(PKG, "_build")
 
-SOURCES = ["gcm_kernels.cu", "gcm_api.cu", "gcm_noalloc.cu", "gfc_fits.cu", "gcm_stream.cu", "gcm_batch.cu"]
+SOURCES = ["gcm_kernels.cu", "gcm_api.cu", "gcm_noalloc.cu", "gfc_fits.cu", "gcm_stream.cu", "gcm_batch.cu", "gcm_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -488,6 +488,7 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
         }
         for (auto e : ctx->spare) cudaEventDestroy(e);
         stream_release(ctx);
+        for (auto k : ctx->keys) cudaFree(k);
         if (ctx->tabs) cudaFree(ctx->tabs);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }

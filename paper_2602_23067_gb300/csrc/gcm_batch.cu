@@ -143,6 +143,7 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
         b.K = K[i];
         b.item_base = base[i];
         b.nr = (uint32_t)m.key_len / 4 + 6;
+        b.dec = decrypt ? 1u : 0u;
         b.km = reinterpret_cast<KeyMat *>(dev + o_km[i]);
         b.mm = reinterpret_cast<MsgMat *>(dev + o_km[i] + sizeof(KeyMat));
         b.partials = reinterpret_cast<gf128 *>(dev + o_part[i]);

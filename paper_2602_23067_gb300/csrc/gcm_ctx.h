@@ -41,6 +41,9 @@ struct gcm_ctx {
     size_t ring_bytes = 0;
     uint8_t *staging = nullptr;     // pinned host staging for tags / status words
     size_t staging_bytes = 0;
+    // registered keys (gcm_key_register)
+    std::vector<gcmgpu::KeyMat *> keys;
+    std::vector<uint32_t> key_nr;
 };
 
 namespace gcmgpu {

@@ -96,7 +96,7 @@ struct BatchMsg {
     uint64_t K;             // tiles of 2^BATCH_TILE_LOG2 blocks
     uint64_t item_base;     // index of the message's first work item
     uint32_t nr;
-    uint32_t pad_;
+    uint32_t dec;           // 1: decrypt-verify this message (GHASH over the input)
     KeyMat *km;
     MsgMat *mm;
     gf128 *partials;        // K entries
@@ -152,6 +152,9 @@ cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream
 cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
                                    const DevTables *tabs, uint64_t *t_start, cudaStream_t stream);
 cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t stream);
+// J0 and E_K(J0) for messages whose key material is already built (cached keys).
+cudaError_t launch_msg_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n, const DevTables *tabs,
+                             cudaStream_t stream);
 cudaError_t launch_batch_zero(const BatchMsg *msgs, uint32_t n, cudaStream_t stream);
 cudaError_t configure_kernels();  // sets the dynamic shared memory limit
 

@@ -760,12 +760,12 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         v.M = v.a_blocks + (bm.len + 15) / 16;
         v.K = bm.K;
         v.tile_log2 = BATCH_TILE_LOG2;
-        v.dec = p.decrypt != 0;
+        v.dec = bm.dec != 0;
         v.km = bm.km;
         v.mm = bm.mm;
         v.partials = bm.partials;
         if (mi != cur) {
-            // New key: its GHASH table and segment factors.
+            // New message: its key's GHASH table and segment factors.
             stage_ghash_table(smem, bm.km);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             if (lane == 0) reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf16[warp];
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         __syncthreads();
         if (s_last) {
             __threadfence();
-            batch_combine(bm, p.decrypt != 0);
+            batch_combine(bm, bm.dec != 0);
         }
     }
 }
@@ -806,6 +806,49 @@ __global__ void __launch_bounds__(256) batch_zero_kernel(const BatchMsg *msgs, u
     uint4 *o = reinterpret_cast<uint4 *>(m.out);
     for (uint64_t i = threadIdx.x; i < nvec; i += blockDim.x) o[i] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x < (m.len & 15)) m.out[nvec * 16 + threadIdx.x] = 0;
+}
+
+// J0 and E_K(J0) for messages whose key material is cached (one thread per
+// message; SP 800-38D Alg. 4 step 2 and the tag's E_K(J0)).
+__global__ void __launch_bounds__(128) msg_setup_kernel(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
+                                                        const DevTables *tabs)
+{
+    __shared__ uint8_t sbox[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = tabs->sbox[i];
+    __syncthreads();
+    const uint32_t mi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= n) return;
+    const BatchMsg &m = msgs[mi];
+    const BatchKey &k = keys[mi];
+    const KeyMat *km = m.km;
+    uint32_t j0[4];
+    if (k.iv_len == 12) {
+        for (int i = 0; i < 3; i++)
+            j0[i] = (uint32_t)k.iv[4 * i] | ((uint32_t)k.iv[4 * i + 1] << 8) | ((uint32_t)k.iv[4 * i + 2] << 16) |
+                    ((uint32_t)k.iv[4 * i + 3] << 24);
+        j0[3] = 0x01000000u;
+    } else {
+        const gf128 H = km->H;
+        gf128 y = gf_zero();
+        for (uint32_t off = 0; off < k.iv_len; off += 16) {
+            uint32_t w[4] = {0u, 0u, 0u, 0u};
+            for (uint32_t b = 0; b < 16 && off + b < k.iv_len; b++) w[b >> 2] |= (uint32_t)k.iv[off + b] << (8 * (b & 3));
+            y = gf_mul(gf_xor(y, gf_from_mem(w[0], w[1], w[2], w[3])), H);
+        }
+        gf128 lb = gf_zero();
+        const uint64_t bits = (uint64_t)k.iv_len * 8u;
+        lb.w[2] = (uint32_t)(bits >> 32);
+        lb.w[3] = (uint32_t)bits;
+        y = gf_mul(gf_xor(y, lb), H);
+        const uint4 jm = gf_to_mem(y);
+        j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
+    }
+    uint32_t e[4];
+    aes_block_bytes(km->rk, (int)km->nr, sbox, j0, e);
+    for (int i = 0; i < 4; i++) {
+        m.mm->j0[i] = j0[i];
+        m.mm->ej0[i] = e[i];
+    }
 }
 
 // Key setup for many messages: one CTA each.
@@ -919,6 +962,14 @@ cudaError_t launch_batch(const BatchParams &p, int grid, cudaStream_t stream)
 {
     if (p.total_items == 0) return cudaSuccess;
     batch_kernel<<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_msg_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n, const DevTables *tabs,
+                             cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    msg_setup_kernel<<<(n + 127) / 128, 128, 0, stream>>>(msgs, keys, n, tabs);
     return cudaGetLastError();
 }
 
