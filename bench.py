@@ -618,6 +618,144 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Poisson arrivals of encrypt / decrypt-verify requests (50/50) on pinned
+    host buffers, sizes lognormal (median 1 MiB, sigma 1.5) clipped to
+    2880 B..256 MiB and rounded up to whole 2880-byte records, 256 cached keys
+    (AES-128/AES-256), 1% of decryptions with one flipped tag bit; the
+    continuous-batching server against a one-request-per-launch server, per
+    arrival rate: p50/p99 latency (arrival to outputs in host memory) and
+    GB/s."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2602_23067_gb300 import Context, workloads
+
+    rank, local, world = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(4)
+    ctx = Context(local)
+    n_keys, n_prep = 256, args.prepared
+    keys = [rng.integers(0, 256, 16 if i % 2 else 32, dtype=np.uint8).tobytes() for i in range(n_keys)]
+    handles = [ctx.key_register(k) for k in keys]
+    sizes = np.clip(rng.lognormal(math.log(1 << 20), 1.5, n_prep), 2880, 256 << 20)
+    sizes = (np.ceil(sizes / 2880) * 2880).astype(np.int64)
+    prep = []
+    total = int(sizes.sum())
+    pt_all = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    ct_all = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    out_all = torch.empty(total, dtype=torch.uint8, pin_memory=True)
+    pt_all.copy_(torch.randint(0, 256, (total,), dtype=torch.uint8, device="cuda"))
+    off = 0
+    batch = []
+    for i in range(n_prep):
+        n = int(sizes[i])
+        k = int(rng.integers(0, n_keys))
+        iv = rng.integers(0, 256, 12, dtype=np.uint8).tobytes()
+        aad = workloads.fits_header(int(rng.integers(0, 1 << 30)), -32, [n // 4, 1], ncards=36)
+        tag = np.zeros(16, np.uint8)
+        prep.append({"n": n, "k": k, "iv": iv, "aad": np.frombuffer(aad, np.uint8).copy(),
+                     "pt": pt_all[off: off + n], "ct": ct_all[off: off + n], "out": out_all[off: off + n],
+                     "tag": tag})
+        batch.append({"key": keys[k], "iv": iv, "aad": prep[-1]["aad"], "inp": pt_all[off: off + n],
+                      "out": ct_all[off: off + n], "tag": tag})
+        off += n
+    ctx.batch(batch)  # pre-encrypt: ciphertexts and tags for the decrypt requests
+    for p in prep:
+        bad = p["tag"].copy()
+        bad[int(rng.integers(0, 16))] ^= np.uint8(1 << int(rng.integers(0, 8)))
+        p["bad"] = bad
+    rates = [int(r) for r in args.rates.split(",")]
+
+    def run_rate(rate, server_kind):
+        if server_kind == "continuous":
+            srv = ctx.server(hbm_budget_bytes=40 * 10 ** 9, max_wave_msgs=4096, max_inflight=3)
+        else:
+            srv = ctx.server(hbm_budget_bytes=40 * 10 ** 9, max_wave_msgs=1, max_inflight=1)
+        count = int(min(args.max_requests, max(2000, rate * args.seconds)))
+        r = np.random.default_rng(rate)
+        gaps = r.exponential(1.0 / rate, count)
+        picks = r.integers(0, n_prep, count)
+        ops = r.integers(0, 2, count)
+        flips = r.random(count) < 0.01
+        from paper_2602_23067_gb300 import _native
+
+        now = _native.lib.gcm_now_ns
+        t0 = now() + 20_000_000
+        arrivals = t0 + np.cumsum(gaps * 1e9).astype(np.int64)
+        lat, done_bytes, auth_ok, auth_bad = [], 0, 0, 0
+        expect_bad = set()
+        outstanding = 0
+        tags = [np.zeros(16, np.uint8) for _ in range(count)]
+        i = 0
+        while i < count or outstanding:
+            tnow = now()
+            while i < count and arrivals[i] <= tnow:
+                p = prep[picks[i]]
+                if ops[i] == 0:
+                    srv.submit(0, handles[p["k"]], p["iv"], p["aad"], p["pt"], p["out"], tags[i],
+                               arrival_ns=int(arrivals[i]), user=i)
+                else:
+                    tg = p["bad"] if flips[i] else p["tag"]
+                    if flips[i]:
+                        expect_bad.add(i)
+                    srv.submit(1, handles[p["k"]], p["iv"], p["aad"], p["ct"], p["out"], tg,
+                               arrival_ns=int(arrivals[i]), user=i)
+                outstanding += 1
+                i += 1
+            for ticket, status, arr, done, user in srv.poll():
+                outstanding -= 1
+                lat.append((done - arr) / 1e6)
+                done_bytes += prep[picks[user]]["n"]
+                if user in expect_bad:
+                    auth_bad += 1 if status == -3 else 0
+                elif status == 0:
+                    auth_ok += 1
+        t_end = now()
+        stats = srv.stats()
+        srv.close()
+        elapsed = (t_end - t0) / 1e9
+        return {"rate_req_s": rate, "requests": count, "achieved_req_s": count / elapsed,
+                "gbs": done_bytes / elapsed / 1e9, "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+                "waves": stats["waves"], "flipped_tags": len(expect_bad), "flipped_rejected": auth_bad,
+                "good_ok": auth_ok, "good_total": count - len(expect_bad)}
+
+    results = {"continuous": [], "per_request": []}
+    for rate in rates:
+        results["continuous"].append(run_rate(rate, "continuous"))
+        results["per_request"].append(run_rate(rate, "per_request"))
+    best = max(results["continuous"], key=lambda x: x["gbs"])
+    line = {
+        "metric": "AES-GCM serving: p50/p99 latency and GB/s under Poisson arrivals, continuous batching vs "
+                  "per-request launch",
+        "value": best["gbs"],
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": len(rates),
+        "warmup": 0,
+        "ms_per_step": None,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "serving_poisson", "rates_req_s": rates, "prepared_messages": n_prep,
+                   "sizes": "lognormal median 1 MiB sigma 1.5, 2880 B..256 MiB, whole 2880-B records",
+                   "keys": "256 cached (AES-128/AES-256)", "ops": "50/50 encrypt / decrypt-verify",
+                   "tamper": "1% of decryptions with one flipped tag bit", "hbm_budget_bytes": 40 * 10 ** 9,
+                   "host_buffers": "pinned"},
+        "serving": results,
+        "e2e": None,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -627,8 +765,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-bytes", type=int, default=8 << 20)
-    ap.add_argument("--workload", choices=["fits4g", "batched"], default="fits4g",
-                    help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages")
+    ap.add_argument("--workload", choices=["fits4g", "batched", "serving"], default="fits4g",
+                    help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages; "
+                         "serving: Poisson request stream")
+    ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving arrival rates (req/s)")
+    ap.add_argument("--seconds", type=float, default=3.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--max-requests", type=int, default=20000, help="serving: cap on requests per rate")
+    ap.add_argument("--prepared", type=int, default=384, help="serving: distinct prepared messages")
     ap.add_argument("--messages", type=int, default=10000, help="messages of the batched workload")
     ap.add_argument("--side", type=int, default=32768,
                     help="image side in pixels (default 32768: the 4 GiB workload; smaller sides are for profiling)")
@@ -642,6 +785,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "serving":
+        return run_serving(args)
     return run_ours(args)
 
 
