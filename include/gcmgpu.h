@@ -214,6 +214,10 @@ int gcm_server_create(gcm_ctx *ctx, size_t hbm_budget_bytes, size_t max_wave_msg
  * alone exceeds the HBM budget. */
 int gcm_server_submit(gcm_server *srv, const gcm_request *req, uint64_t *ticket);
 
+/* Queues n requests at once (same rules as gcm_server_submit; all or none
+ * are queued).  Their tickets are first_ticket, first_ticket + 1, ... */
+int gcm_server_submit_batch(gcm_server *srv, const gcm_request *reqs, size_t n, uint64_t *first_ticket);
+
 /* Moves up to max completions into out; returns how many. */
 size_t gcm_server_poll(gcm_server *srv, gcm_completion *out, size_t max);
 

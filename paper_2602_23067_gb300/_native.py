@@ -95,6 +95,7 @@ SIGNATURES = {
     "gcm_server_create": (ctypes.c_int, [_VP, _SZ, _SZ, ctypes.c_int, ctypes.POINTER(_VP)]),
     "gcm_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(GcmRequest), ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_server_poll": (ctypes.c_size_t, [_VP, ctypes.POINTER(GcmCompletion), _SZ]),
+    "gcm_server_submit_batch": (ctypes.c_int, [_VP, _VP, _SZ, ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "gcm_server_destroy": (None, [_VP]),

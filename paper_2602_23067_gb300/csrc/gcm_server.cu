@@ -468,6 +468,40 @@ int gcm_server_submit(gcm_server *S, const gcm_request *r, uint64_t *ticket)
     return GCM_OK;
 }
 
+int gcm_server_submit_batch(gcm_server *S, const gcm_request *reqs, size_t n, uint64_t *first_ticket)
+{
+    if (!S || (n && !reqs)) return ctx_fail(GCM_ERR_INVALID_ARG, "server or requests are NULL");
+    std::vector<Pending> ps(n);
+    for (size_t i = 0; i < n; i++) {
+        const gcm_request *r = &reqs[i];
+        if (r->op != 0 && r->op != 1) return ctx_fail(GCM_ERR_INVALID_ARG, "op must be 0 (encrypt) or 1 (decrypt-verify)");
+        if (r->key >= S->ctx->keys.size()) return ctx_fail(GCM_ERR_INVALID_ARG, "unknown key handle");
+        if (!r->iv || r->iv_len == 0 || r->iv_len > 65536) return ctx_fail(GCM_ERR_INVALID_ARG, "IV must be 1..65536 bytes");
+        if (r->len > (1ull << 36) - 32) return ctx_fail(GCM_ERR_LENGTH_LIMIT, "payload too long");
+        if (r->len && (!r->in || !r->out)) return ctx_fail(GCM_ERR_INVALID_ARG, "payload pointer is NULL");
+        if (r->aad_len && !r->aad) return ctx_fail(GCM_ERR_INVALID_ARG, "aad is NULL with a nonzero length");
+        if (!r->tag) return ctx_fail(GCM_ERR_INVALID_ARG, "tag pointer is NULL");
+        if (request_bytes(*r) > S->budget) return ctx_fail(GCM_ERR_NO_MEMORY, "request larger than the server's HBM budget");
+        Pending &p = ps[i];
+        p.r = *r;
+        p.t_arrival = r->arrival_ns ? r->arrival_ns : now_ns();
+        p.iv.assign(r->iv, r->iv + r->iv_len);
+        if (r->op == 1) memcpy(p.tag_in, r->tag, 16);
+        else memset(p.tag_in, 0, 16);
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->queue.size() + n > S->queue_cap) return ctx_fail(GCM_ERR_BUSY, "server queue full");
+        if (first_ticket) *first_ticket = S->next_ticket.load();
+        for (size_t i = 0; i < n; i++) {
+            ps[i].ticket = S->next_ticket++;
+            S->queue.push_back(std::move(ps[i]));
+        }
+    }
+    S->cv.notify_one();
+    return GCM_OK;
+}
+
 size_t gcm_server_poll(gcm_server *S, gcm_completion *out, size_t max)
 {
     if (!S || !out) return 0;
