@@ -158,6 +158,16 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
 int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
                     int32_t *status, uint64_t *done_ns, void *stream);
 
+/* How host buffers (GCM_MEM_HOST, host batches, the server) reach the GPU.
+ * mode 0 (default, auto): when the device can access host memory directly
+ *   (cudaDevAttrPageableMemoryAccess, e.g. Grace-Blackwell over NVLink-C2C
+ *   with address translation), the kernels read the host input and write
+ *   the host output themselves -- no copies, no staging -- for buffers that
+ *   are 16-byte aligned; otherwise the staged pipeline below is used.
+ * mode 1: require direct access (GCM_ERR_INVALID_ARG if unsupported).
+ * mode 2: always stage through device chunk buffers. */
+int gcm_ctx_set_host_access(gcm_ctx *ctx, int mode);
+
 /* Host-mode streaming geometry: chunk_bytes of payload per chunk (rounded
  * to whole tiles) and n_buffers device chunk buffers in the ring (>= 2).
  * Defaults: 256 MiB and 3. */
@@ -226,6 +236,11 @@ size_t gcm_server_poll(gcm_server *srv, gcm_completion *out, size_t max);
  * server. */
 int gcm_server_stats(gcm_server *srv, uint64_t *waves, uint64_t *messages, size_t *queued,
                      size_t *bytes_in_flight);
+
+/* Time spent so far, summed over waves (ms): out[0] host time issuing
+ * waves, out[1] copy-in stage, out[2] compute stage (from copy-in done to
+ * kernels done, queueing included), out[3] copy-out stage. */
+int gcm_server_timing(gcm_server *srv, double out[4]);
 
 /* Finishes the queued requests, stops the thread, frees the server. */
 void gcm_server_destroy(gcm_server *srv);

@@ -91,6 +91,7 @@ SIGNATURES = {
     "gcm_batch": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int, _VP]),
     "gcm_ctx_set_streaming": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
+    "gcm_ctx_set_host_access": (ctypes.c_int, [_VP, ctypes.c_int]),
     "gcm_key_register": (ctypes.c_int, [_VP, _VP, _SZ, ctypes.POINTER(ctypes.c_uint32)]),
     "gcm_server_create": (ctypes.c_int, [_VP, _SZ, _SZ, ctypes.c_int, ctypes.POINTER(_VP)]),
     "gcm_server_submit": (ctypes.c_int, [_VP, ctypes.POINTER(GcmRequest), ctypes.POINTER(ctypes.c_uint64)]),
@@ -99,6 +100,7 @@ SIGNATURES = {
     "gcm_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "gcm_server_destroy": (None, [_VP]),
+    "gcm_server_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
     "gcm_now_ns": (ctypes.c_uint64, []),
     "gcm_batch_timed": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_uint64), _VP]),

@@ -177,6 +177,11 @@ class Context:
         return pt
 
     # -- many messages (gcm_batch) ------------------------------------------
+    def set_host_access(self, mode: int) -> None:
+        """0 auto (direct kernel access to host memory when the device supports
+        it), 1 require direct, 2 always stage through device buffers."""
+        check(lib.gcm_ctx_set_host_access(self.handle, mode))
+
     def set_streaming(self, chunk_bytes: int, n_buffers: int = 3) -> None:
         check(lib.gcm_ctx_set_streaming(self.handle, chunk_bytes, n_buffers))
 

@@ -5,6 +5,7 @@
 // gcm_kernels.cu.  Every step of the method runs on the device.
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -263,6 +264,45 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
 {
     int rc = check_common(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, tag, mem);
     if (rc) return rc;
+    const bool aligned = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
+    if (mem == GCM_MEM_HOST && ctx->host_direct && aligned) {
+        // The kernels read the host buffers and write the host output
+        // directly over the CPU-GPU link; only the tag / verdict pass
+        // through device scratch.
+        DeviceGuard guard(ctx->device);
+        if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        Scratch io;
+        rc = scratch_alloc(ctx, 256, s, io);
+        if (rc) return rc;
+        uint8_t *iob = static_cast<uint8_t *>(io.base);
+        int32_t *d_status = reinterpret_cast<int32_t *>(iob);
+        uint8_t *d_tag = iob + 64;
+        cudaError_t e = cudaSuccess;
+        if (decrypt) e = cudaMemcpyAsync(d_tag, tag, 16, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            scratch_free(ctx, io, s);
+            return cuda_fail(e, "tag copy");
+        }
+        Scratch sc;
+        rc = enqueue_device(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, d_tag, decrypt, d_status, sc, s);
+        if (rc) {
+            if (sc.base) scratch_free(ctx, sc, s);
+            scratch_free(ctx, io, s);
+            return rc;
+        }
+        scratch_free(ctx, sc, s);
+        int32_t status = 0;
+        uint8_t htag[16];
+        e = cudaMemcpyAsync(decrypt ? (void *)&status : (void *)htag, decrypt ? (void *)d_status : (void *)d_tag,
+                            decrypt ? sizeof(int32_t) : 16, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        scratch_free(ctx, io, s);
+        if (e != cudaSuccess) return cuda_fail(e, "host-direct call");
+        if (!decrypt) memcpy(tag, htag, 16);
+        if (decrypt && status != 0) return fail(GCM_ERR_AUTH, "authentication tag mismatch: output zero-filled");
+        return GCM_OK;
+    }
     if (mem == GCM_MEM_HOST) {
         // Host buffers are streamed through the context's chunk ring.
         gcm_msg m;
@@ -384,6 +424,12 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     ctx->device = device;
     ctx->budget = hbm_budget_bytes;
     e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) {
+        int pageable = 0;
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
+        const char *force = getenv("GCMGPU_HOST_STAGING");
+        ctx->host_direct = pageable != 0 && !(force && force[0] == '1');
+    }
     if (e == cudaSuccess) e = configure_kernels();
     if (e == cudaSuccess) {
         cudaMemPoolProps props;
@@ -409,6 +455,20 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     return GCM_OK;
 }
 
+int gcm_ctx_set_host_access(gcm_ctx *ctx, int mode)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (mode < 0 || mode > 2) return fail(GCM_ERR_INVALID_ARG, "mode must be 0 (auto), 1 (direct) or 2 (staged)");
+    int pageable = 0;
+    {
+        DeviceGuard g(ctx->device);
+        cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, ctx->device);
+    }
+    if (mode == 1 && !pageable) return fail(GCM_ERR_INVALID_ARG, "the device cannot access host memory directly");
+    ctx->host_direct = (mode == 2) ? false : (pageable != 0);
+    return GCM_OK;
+}
+
 int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers)
 {
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
@@ -424,7 +484,26 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t 
 {
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
     if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
-    if (mem == GCM_MEM_HOST) return stream_host(ctx, msgs, n, decrypt != 0, status);
+    if (mem == GCM_MEM_HOST) {
+        bool aligned = true;
+        for (size_t i = 0; i < n && aligned; i++)
+            aligned = ((((uintptr_t)msgs[i].in) | ((uintptr_t)msgs[i].out)) & 15u) == 0;
+        if (ctx->host_direct && aligned) {
+            // One persistent launch straight over the host buffers.
+            cudaStream_t s = nullptr;
+            {
+                std::lock_guard<std::mutex> lk(ctx->stream_mu);
+                if (!ctx->s_comp) {
+                    DeviceGuard g(ctx->device);
+                    cudaError_t e = cudaStreamCreateWithFlags(&ctx->s_comp, cudaStreamNonBlocking);
+                    if (e != cudaSuccess) return cuda_fail(e, "creating a stream");
+                }
+                s = ctx->s_comp;
+            }
+            return batch_device(ctx, msgs, n, decrypt != 0, status, nullptr, s);
+        }
+        return stream_host(ctx, msgs, n, decrypt != 0, status);
+    }
     if (mem == GCM_MEM_DEVICE)
         return batch_device(ctx, msgs, n, decrypt != 0, status, nullptr, static_cast<cudaStream_t>(stream));
     return fail(GCM_ERR_INVALID_ARG, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");

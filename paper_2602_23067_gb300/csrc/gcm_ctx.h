@@ -15,6 +15,10 @@
 struct gcm_ctx {
     int device = 0;
     int num_sms = 0;
+    // Host buffers are read and written by the kernels themselves over the
+    // CPU-GPU link (coherent access, e.g. NVLink-C2C with address translation)
+    // instead of being copied through device staging buffers.
+    bool host_direct = false;
     size_t budget = 0;          // 0 = unlimited
     size_t in_flight = 0;       // scratch bytes held by calls not yet returned
     cudaMemPool_t pool = nullptr;

@@ -495,12 +495,24 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
             const uint32_t nwin = (seg_len + (c_lo & 31u) + 31u) >> 5;
             const uint4 *in = reinterpret_cast<const uint4 *>(v.in) + j_lo;
             uint4 *out = reinterpret_cast<uint4 *>(v.out) + j_lo;
+            // The next window's input is loaded one window ahead, so a load's
+            // latency (long when the payload is in host memory across the
+            // CPU-GPU link) overlaps a window of AES work.
+            uint4 din_next = make_uint4(0u, 0u, 0u, 0u);
+            {
+                const uint32_t d0 = W0 + lane - c_lo;
+                if (d0 < seg_len) din_next = __ldcs(in + d0);
+            }
             for (uint32_t wi = 0; wi < nwin; wi++) {
                 const uint32_t W = W0 + (wi << 5);
                 const uint32_t d = W + lane - c_lo;
                 const bool active = d < seg_len;
-                uint4 din = make_uint4(0u, 0u, 0u, 0u);
-                if (active) din = __ldcs(in + d);
+                const uint4 din = din_next;
+                // The offset is formed in 32-bit arithmetic first: for lanes
+                // before the segment start d has wrapped and d + 32 is their
+                // (small) offset in the next window.
+                const uint32_t dn = d + 32u;
+                if (dn < seg_len) din_next = __ldcs(in + dn);
                 if ((W >> 8) != gc.grp) {
                     // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
                     gc.grp = W >> 8;

@@ -63,6 +63,11 @@ struct Wave {
 
 }  // namespace
 
+struct gcm_server;
+namespace {
+bool is_direct(const gcm_server *S, const gcm_request &r);
+}
+
 struct gcm_server {
     gcm_ctx *ctx = nullptr;
     size_t budget = 0;
@@ -71,8 +76,10 @@ struct gcm_server {
     cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
     std::vector<uint8_t *> stages;  // one pinned staging buffer per in-flight slot
     size_t stage_bytes = 0;
-    std::vector<cudaEvent_t> ev_in, ev_comp, ev_done;
+    std::vector<cudaEvent_t> ev_start, ev_in, ev_comp, ev_done;
     std::vector<bool> slot_busy;
+    // timing of the pipeline stages (summed over waves)
+    double t_launch_host_ms = 0, t_in_ms = 0, t_comp_ms = 0, t_out_ms = 0;
 
     std::mutex mu;
     std::condition_variable cv;
@@ -89,13 +96,23 @@ struct gcm_server {
 
 namespace {
 
+bool is_direct(const gcm_server *S, const gcm_request &r)
+{
+    return S->ctx->host_direct && ((((uintptr_t)r.in) | ((uintptr_t)r.out)) & 15u) == 0;
+}
+
+// Whether the kernels work on this request's host buffers in place (the
+// device reaches host memory directly and the payload is 16-byte aligned).
+bool is_direct(const gcm_server *S, const gcm_request &r);
+
 // Device bytes a request needs inside a wave arena.
-size_t request_bytes(const gcm_request &r)
+size_t request_bytes(const gcm_server *S, const gcm_request &r)
 {
     const uint64_t M = (r.aad_len + 15) / 16 + (r.len + 15) / 16;
     uint64_t K = (M + (1ull << BATCH_TILE_LOG2) - 1) >> BATCH_TILE_LOG2;
     if (K == 0) K = 1;
-    return al(r.len) + al(r.aad_len) + al(sizeof(MsgMat)) + al(K * sizeof(gf128)) + al((K / 2 + 1) * sizeof(gf128)) +
+    const size_t data = is_direct(S, r) ? 0 : al(r.len) + al(r.aad_len);
+    return data + al(sizeof(MsgMat)) + al(K * sizeof(gf128)) + al((K / 2 + 1) * sizeof(gf128)) +
            al(sizeof(BatchMsg) + sizeof(BatchKey) + 64) + 64;
 }
 
@@ -144,10 +161,12 @@ int launch_wave(gcm_server *S, Wave &w)
         off = al(off + k * sizeof(gf128));
         o_tree[i] = off;
         off = al(off + (k / 2 + 1) * sizeof(gf128));
-        o_pay[i] = off;
-        off = al(off + r.len);
-        o_aad[i] = off;
-        off = al(off + r.aad_len);
+        if (!is_direct(S, r)) {
+            o_pay[i] = off;
+            off = al(off + r.len);
+            o_aad[i] = off;
+            off = al(off + r.aad_len);
+        }
     }
     w.arena_bytes = off;
     cudaError_t e = cudaMallocFromPoolAsync(reinterpret_cast<void **>(&w.arena), off, ctx->pool, S->s_in);
@@ -165,9 +184,15 @@ int launch_wave(gcm_server *S, Wave &w)
         const KeyMat *km = ctx->keys[r.key];
         BatchMsg &b = hm[i];
         memset(&b, 0, sizeof(b));
-        b.in = dev + o_pay[i];
-        b.out = dev + o_pay[i];
-        b.aad = dev + o_aad[i];
+        if (is_direct(S, r)) {
+            b.in = r.in;
+            b.out = r.out;
+            b.aad = r.aad;
+        } else {
+            b.in = dev + o_pay[i];
+            b.out = dev + o_pay[i];
+            b.aad = dev + o_aad[i];
+        }
         b.len = r.len;
         b.aad_len = r.aad_len;
         b.K = K[i];
@@ -189,9 +214,11 @@ int launch_wave(gcm_server *S, Wave &w)
         memcpy(st + o_exp + 16 * i, p.tag_in, 16);
     }
     // Copy-in stream: descriptors, payloads, AADs.
+    cudaEventRecord(S->ev_start[w.slot], S->s_in);
     e = cudaMemcpyAsync(dev, st, host_bytes, cudaMemcpyHostToDevice, S->s_in);
     for (size_t i = 0; i < n && e == cudaSuccess; i++) {
         const gcm_request &r = w.reqs[i].r;
+        if (is_direct(S, r)) continue;
         if (r.len) e = cudaMemcpyAsync(dev + o_pay[i], r.in, r.len, cudaMemcpyHostToDevice, S->s_in);
         if (e == cudaSuccess && r.aad_len) e = cudaMemcpyAsync(dev + o_aad[i], r.aad, r.aad_len, cudaMemcpyHostToDevice, S->s_in);
     }
@@ -220,6 +247,7 @@ int launch_wave(gcm_server *S, Wave &w)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(S->s_out, S->ev_comp[w.slot], 0);
     for (size_t i = 0; i < n && e == cudaSuccess; i++) {
         const gcm_request &r = w.reqs[i].r;
+        if (is_direct(S, r)) continue;
         if (r.len) e = cudaMemcpyAsync(r.out, dev + o_pay[i], r.len, cudaMemcpyDeviceToHost, S->s_out);
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(st + host_bytes, dev + o_ret, 32 * n, cudaMemcpyDeviceToHost, S->s_out);
@@ -239,7 +267,14 @@ void finish_wave(gcm_server *S, Wave &w)
     host_bytes = al(host_bytes + 16 * n);
     const uint8_t *ret = w.stage + host_bytes;
     const uint64_t t = now_ns();
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, S->ev_start[w.slot], S->ev_in[w.slot]);
+    cudaEventElapsedTime(&b, S->ev_in[w.slot], S->ev_comp[w.slot]);
+    cudaEventElapsedTime(&c, S->ev_comp[w.slot], w.done);
     std::lock_guard<std::mutex> lk(S->mu);
+    S->t_in_ms += a;
+    S->t_comp_ms += b;
+    S->t_out_ms += c;
     for (size_t i = 0; i < n; i++) {
         const Pending &p = w.reqs[i];
         int32_t status;
@@ -257,7 +292,7 @@ void finish_wave(gcm_server *S, Wave &w)
         c.complete_ns = t;
         c.user = p.r.user;
         S->completions.push_back(c);
-        S->bytes_in_flight -= request_bytes(p.r);
+        S->bytes_in_flight -= request_bytes(S, p.r);
     }
     S->slot_busy[w.slot] = false;
 }
@@ -303,7 +338,7 @@ void worker_loop(gcm_server *S)
             }
             size_t ivt = 0;
             while (n < pending.size() && n < S->max_wave) {
-                const size_t b = request_bytes(pending[n].r);
+                const size_t b = request_bytes(S, pending[n].r);
                 const size_t m = n + 1, iv2 = ivt + pending[n].iv.size();
                 const size_t sn = al(m * sizeof(BatchMsg)) + al(m * sizeof(BatchKey)) + al(iv2) + al(16 * m) + 32 * m;
                 if (wave_bytes + b > avail || sn > S->stage_bytes) break;
@@ -324,7 +359,10 @@ void worker_loop(gcm_server *S)
                 S->bytes_in_flight += wave_bytes;
                 S->slot_busy[slot] = true;
             }
-            if (launch_wave(S, w) != GCM_OK) {
+            const uint64_t th0 = now_ns();
+            const int lrc = launch_wave(S, w);
+            S->t_launch_host_ms += (now_ns() - th0) / 1e6;
+            if (lrc != GCM_OK) {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->fatal = GCM_ERR_CUDA;
                 for (auto &p : w.reqs) {
@@ -335,7 +373,7 @@ void worker_loop(gcm_server *S)
                     c.complete_ns = now_ns();
                     c.user = p.r.user;
                     S->completions.push_back(c);
-                    S->bytes_in_flight -= request_bytes(p.r);
+                    S->bytes_in_flight -= request_bytes(S, p.r);
                 }
                 S->slot_busy[slot] = false;
                 continue;
@@ -421,10 +459,12 @@ int gcm_server_create(gcm_ctx *ctx, size_t hbm_budget_bytes, size_t max_wave_msg
         e = cudaMallocHost(reinterpret_cast<void **>(&st), S->stage_bytes);
         if (e != cudaSuccess) break;
         S->stages.push_back(st);
-        cudaEvent_t a, b, c;
-        e = cudaEventCreateWithFlags(&a, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b, cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c, cudaEventDisableTiming);
+        cudaEvent_t a, b, c, d;
+        e = cudaEventCreate(&a);
+        if (e == cudaSuccess) e = cudaEventCreate(&b);
+        if (e == cudaSuccess) e = cudaEventCreate(&c);
+        if (e == cudaSuccess) e = cudaEventCreate(&d);
+        S->ev_start.push_back(d);
         S->ev_in.push_back(a);
         S->ev_comp.push_back(b);
         S->ev_done.push_back(c);
@@ -450,7 +490,7 @@ int gcm_server_submit(gcm_server *S, const gcm_request *r, uint64_t *ticket)
     if (r->len && (!r->in || !r->out)) return ctx_fail(GCM_ERR_INVALID_ARG, "payload pointer is NULL");
     if (r->aad_len && !r->aad) return ctx_fail(GCM_ERR_INVALID_ARG, "aad is NULL with a nonzero length");
     if (!r->tag) return ctx_fail(GCM_ERR_INVALID_ARG, "tag pointer is NULL");
-    if (request_bytes(*r) > S->budget) return ctx_fail(GCM_ERR_NO_MEMORY, "request larger than the server's HBM budget");
+    if (request_bytes(S, *r) > S->budget) return ctx_fail(GCM_ERR_NO_MEMORY, "request larger than the server's HBM budget");
     Pending p;
     p.r = *r;
     p.t_arrival = r->arrival_ns ? r->arrival_ns : now_ns();
@@ -481,7 +521,7 @@ int gcm_server_submit_batch(gcm_server *S, const gcm_request *reqs, size_t n, ui
         if (r->len && (!r->in || !r->out)) return ctx_fail(GCM_ERR_INVALID_ARG, "payload pointer is NULL");
         if (r->aad_len && !r->aad) return ctx_fail(GCM_ERR_INVALID_ARG, "aad is NULL with a nonzero length");
         if (!r->tag) return ctx_fail(GCM_ERR_INVALID_ARG, "tag pointer is NULL");
-        if (request_bytes(*r) > S->budget) return ctx_fail(GCM_ERR_NO_MEMORY, "request larger than the server's HBM budget");
+        if (request_bytes(S, *r) > S->budget) return ctx_fail(GCM_ERR_NO_MEMORY, "request larger than the server's HBM budget");
         Pending &p = ps[i];
         p.r = *r;
         p.t_arrival = r->arrival_ns ? r->arrival_ns : now_ns();
@@ -525,6 +565,17 @@ int gcm_server_stats(gcm_server *S, uint64_t *waves, uint64_t *messages, size_t 
     return S->fatal;
 }
 
+int gcm_server_timing(gcm_server *S, double out[4])
+{
+    if (!S || !out) return ctx_fail(GCM_ERR_INVALID_ARG, "server or out is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out[0] = S->t_launch_host_ms;
+    out[1] = S->t_in_ms;
+    out[2] = S->t_comp_ms;
+    out[3] = S->t_out_ms;
+    return GCM_OK;
+}
+
 void gcm_server_destroy(gcm_server *S)
 {
     if (!S) return;
@@ -538,6 +589,7 @@ void gcm_server_destroy(gcm_server *S)
     if (S->s_comp) cudaStreamSynchronize(S->s_comp);
     if (S->s_out) cudaStreamSynchronize(S->s_out);
     for (auto p : S->stages) cudaFreeHost(p);
+    for (auto e : S->ev_start) cudaEventDestroy(e);
     for (auto e : S->ev_in) cudaEventDestroy(e);
     for (auto e : S->ev_comp) cudaEventDestroy(e);
     for (auto e : S->ev_done) cudaEventDestroy(e);

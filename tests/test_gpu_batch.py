@@ -105,13 +105,18 @@ def test_batch_device_decrypt_rejects_only_the_tampered(env):
             assert got == m["pt"]
 
 
-def test_batch_host_streaming_small_chunks(env):
+@pytest.mark.parametrize("host_access", [2, 0])
+def test_batch_host_streaming_small_chunks(env, host_access):
+    """host_access 2: staged through a ring of 3 device chunk buffers of
+    64 KiB (many chunks per message); 0: the kernels work on the host
+    buffers directly when the device can reach host memory."""
     torch, ctx = env
     from paper_2602_23067_gb300 import Context
 
     c2 = Context(0)
     try:
-        c2.set_streaming(64 * 1024, 3)  # many chunks per message, ring of 3
+        c2.set_host_access(host_access)
+        c2.set_streaming(64 * 1024, 3)
         msgs = make_mix(33, 25, median=150000, sigma=1.0, hi=2 << 20)
         hm = []
         for m in msgs:
@@ -141,12 +146,14 @@ def test_batch_host_streaming_small_chunks(env):
         c2.close()
 
 
-def test_host_mode_single_message_many_chunks(env):
+@pytest.mark.parametrize("host_access", [2, 0])
+def test_host_mode_single_message_many_chunks(env, host_access):
     torch, ctx = env
     from paper_2602_23067_gb300 import Context
 
     c2 = Context(0)
     try:
+        c2.set_host_access(host_access)
         c2.set_streaming(128 * 1024, 2)
         key, iv = bytes(range(16)), bytes(range(12))
         aad = workloads.random_bytes(5, 3000).tobytes()

@@ -178,7 +178,9 @@ def test_in_place(torch_cuda, ctx):
     assert to_bytes(buf) == pt
 
 
-def test_host_mode(torch_cuda, ctx):
+@pytest.mark.parametrize("host_access", [0, 2])
+def test_host_mode(torch_cuda, ctx, host_access):
+    ctx.set_host_access(host_access)
     r = random.Random(7000)
     key, iv, aad = rnd(r, 32), rnd(r, 12), rnd(r, 2880)
     pt = workloads.random_bytes(7001, 300000).tobytes()
@@ -191,8 +193,11 @@ def test_host_mode(torch_cuda, ctx):
 
     bad = bytearray(tag)
     bad[0] ^= 1
+    out = np.full(len(pt), 7, np.uint8)
     with pytest.raises(GcmError):
-        ctx.decrypt_verify_host(key, iv, aad, ct, bytes(bad))
+        ctx.decrypt_verify_host(key, iv, aad, ct, bytes(bad), pt=out)
+    assert not out.any()  # payload suppressed in host memory
+    ctx.set_host_access(0)
 
 
 def test_fits_shaped_file(torch_cuda, ctx):

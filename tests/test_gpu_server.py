@@ -72,9 +72,11 @@ def _run(ctx, reqs, handles, max_wave, max_inflight, spread_s=0.0):
         srv.close()
 
 
-@pytest.mark.parametrize("max_wave,max_inflight,spread", [(64, 3, 0.0), (8, 2, 0.0005), (1, 1, 0.0)])
-def test_server_results_match_the_oracle(env, max_wave, max_inflight, spread):
+@pytest.mark.parametrize("max_wave,max_inflight,spread,host_access",
+                         [(64, 3, 0.0, 0), (8, 2, 0.0005, 0), (1, 1, 0.0, 0), (64, 3, 0.0, 2), (8, 2, 0.0005, 2)])
+def test_server_results_match_the_oracle(env, max_wave, max_inflight, spread, host_access):
     torch, ctx = env
+    ctx.set_host_access(host_access)
     keys = [bytes(range(16)), bytes(range(32)), bytes(range(50, 82)), bytes(range(7, 23))]
     handles = [ctx.key_register(k) for k in keys]
     reqs = _requests(41, 48, keys)
@@ -94,6 +96,7 @@ def test_server_results_match_the_oracle(env, max_wave, max_inflight, spread):
             assert out[: len(q["ct"])].tobytes() == q["pt"]
     if max_wave > 1 and spread == 0.0:
         assert stats["waves"] < len(reqs)  # requests were batched
+    ctx.set_host_access(0)
 
 
 def test_server_rejects_bad_requests(env):
@@ -101,10 +104,28 @@ def test_server_rejects_bad_requests(env):
     from paper_2602_23067_gb300 import GcmError
 
     h = ctx.key_register(bytes(16))
+    big = np.zeros(2 << 20, np.uint8)
+    out = np.zeros(2 << 20, np.uint8)
+    ctx.set_host_access(2)  # staged: the payload must fit the device budget
+    try:
+        with ctx.server(hbm_budget_bytes=1 << 20) as srv:
+            with pytest.raises(GcmError):
+                srv.submit(0, h + 100, bytes(12), None, np.zeros(16, np.uint8), np.zeros(16, np.uint8),
+                           np.zeros(16, np.uint8))
+            with pytest.raises(GcmError) as e:
+                srv.submit(0, h, bytes(12), None, big, out, np.zeros(16, np.uint8))
+            assert e.value.code == -4
+    finally:
+        ctx.set_host_access(0)
+    # direct host access keeps the payload in host memory, so it fits
     with ctx.server(hbm_budget_bytes=1 << 20) as srv:
-        with pytest.raises(GcmError):
-            srv.submit(0, h + 100, bytes(12), None, np.zeros(16, np.uint8), np.zeros(16, np.uint8), np.zeros(16, np.uint8))
-        big = np.zeros(2 << 20, np.uint8)
-        with pytest.raises(GcmError) as e:
-            srv.submit(0, h, bytes(12), None, big, big, np.zeros(16, np.uint8))
-        assert e.value.code == -4
+        tag = np.zeros(16, np.uint8)
+        srv.submit(0, h, bytes(12), None, big, out, tag)
+        deadline = time.time() + 30
+        done = []
+        while not done and time.time() < deadline:
+            done = srv.poll()
+            time.sleep(0.001)
+        assert done and done[0][1] == 0
+        ref_ct, ref_tag = oracle.gcm_encrypt(bytes(16), bytes(12), b"", big.tobytes())
+        assert tag.tobytes() == ref_tag and out.tobytes() == ref_ct
