@@ -110,6 +110,34 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                        uint8_t *pt, int mem, void *stream);
 
 /* ---------------------------------------------------------------- */
+/* The two halves of the fused pass on their own                    */
+/* ---------------------------------------------------------------- */
+
+/* CTR keystream XOR alone (SP 800-38D GCTR started at inc32(J0), the
+ * ciphertext half of GCM-AE; the paper's CTR kernel, Sec. 3.3.2, and its
+ * unauthenticated CTR comparison in Sec. 5).  out = in xor E_K(inc32^i(J0)),
+ * byte for byte the ciphertext gcm_encrypt would write; no tag.  Same key
+ * and IV rules as gcm_encrypt.  in/out are DEVICE pointers, 16-byte aligned,
+ * out may equal in; key and iv are host pointers.  Enqueues on `stream` and
+ * returns.  Applying it twice with the same key and IV restores the input. */
+int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+                const uint8_t *iv, size_t iv_len,
+                const uint8_t *in, size_t len, uint8_t *out, void *stream);
+
+/* GHASH alone (SP 800-38D Sec. 6.4 / Algorithm 2 over A || 0^v || C || 0^u ||
+ * [len(A)]_64 || [len(C)]_64, with H = E_K(0^128); the paper's GHASH-only
+ * throughput measurement, Sec. 5.2.3).  Runs the same parallel reduction as
+ * the fused pass -- per-chunk Horner, H-power table, log-depth combine
+ * (Sec. 3.3.2, Fig. 2) -- but no AES on the payload and no payload output.
+ * out16 receives the 16-byte GHASH value S, so that the GCM tag of the same
+ * (A, C) is S xor E_K(J0).  aad, data and out16 are DEVICE pointers (data
+ * 16-byte aligned); key is a host pointer.  Enqueues on `stream` and
+ * returns. */
+int gcm_ghash(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
+              const uint8_t *aad, size_t aad_len,
+              const uint8_t *data, size_t len, uint8_t *out16, void *stream);
+
+/* ---------------------------------------------------------------- */
 /* Many messages: batched device launch and streamed host catalogs   */
 /* ---------------------------------------------------------------- */
 

@@ -141,6 +141,36 @@ class Context:
                                  _stream_handle(stream)))
         return pt
 
+    def ctr_xor_device(self, key: bytes, iv: bytes, inp, out=None, stream=None):
+        """Enqueue the CTR keystream XOR alone (gcm_ctr_xor); returns out."""
+        import torch
+
+        if out is None:
+            out = torch.empty_like(inp)
+        kp, kl, kk = _host_buf(key)
+        ip, il, ik = _host_buf(iv)
+        sp, sl = _dev_buf(inp)
+        op, ol = _dev_buf(out)
+        if ol < sl:
+            raise ValueError("output buffer too small")
+        check(lib.gcm_ctr_xor(self.handle, kp, kl, ip, il, sp, sl, op, _stream_handle(stream)))
+        return out
+
+    def ghash_device(self, key: bytes, aad, data, out=None, stream=None):
+        """Enqueue GHASH_H(aad, data) alone (gcm_ghash); returns a 16-byte tensor."""
+        import torch
+
+        if out is None:
+            out = torch.empty(16, dtype=torch.uint8, device=data.device)
+        kp, kl, kk = _host_buf(key)
+        ap, al = _dev_buf(aad)
+        dp, dl = _dev_buf(data)
+        op, ol = _dev_buf(out)
+        if ol < 16:
+            raise ValueError("output buffer too small")
+        check(lib.gcm_ghash(self.handle, kp, kl, ap, al, dp, dl, op, _stream_handle(stream)))
+        return out
+
     # -- host-resident data (bytes / numpy / pinned CPU tensors) ------------
     def encrypt_host(self, key: bytes, iv: bytes, aad, pt, ct=None, stream=0) -> Tuple[object, bytes]:
         """GCM-AE of host data, staged through the device; returns (ct, tag)."""

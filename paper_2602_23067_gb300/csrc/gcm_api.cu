@@ -140,9 +140,12 @@ int check_common(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t
 // Enqueues the whole device path for one message whose aad/in/out/tag live
 // in device memory.  For decryption `tag_dev` is the expected tag and
 // `status_dev` receives 0 or GCM_ERR_AUTH; for encryption the tag is written.
+// mode 1 (CTR only) writes out = in xor keystream and no tag; mode 2 (GHASH
+// only) writes GHASH_H(aad, in) to tag_dev and no payload output.
 int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
                    const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out,
-                   uint8_t *tag_dev, bool decrypt, int32_t *status_dev, Scratch &sc, cudaStream_t s)
+                   uint8_t *tag_dev, bool decrypt, int32_t *status_dev, Scratch &sc, cudaStream_t s,
+                   int mode = 0)
 {
     const uint64_t a_blocks = (aad_len + 15) / 16;
     const uint64_t n_blocks = (len + 15) / 16;
@@ -217,14 +220,16 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         ev1 = take_event(ctx);
     }
     if (prof) cudaEventRecord(ev0, s);
-    e = launch_fused(kf, nr, grid, s);
+    e = launch_fused(kf, nr, grid, s, mode);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     if (prof) {
         cudaEventRecord(ev1, s);
         std::lock_guard<std::mutex> lk(ctx->mu);
-        ctx->timed.push_back({ev0, ev1, (uint64_t)len * 2u + (uint64_t)aad_len});
+        const uint64_t moved = (mode == 2 ? (uint64_t)len : (uint64_t)len * 2u) + (mode == 1 ? 0u : (uint64_t)aad_len);
+        ctx->timed.push_back({ev0, ev1, moved});
     }
     ctx->launches += (K > 0) ? 1 : 0;
+    if (mode == 1) return GCM_OK;  // CTR only: no authenticator
 
     KcParams kc;
     memset(&kc, 0, sizeof(kc));
@@ -239,6 +244,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kc.tag_out = decrypt ? nullptr : tag_dev;
     kc.tag_expected = decrypt ? tag_dev : nullptr;
     kc.status = status_dev;
+    kc.raw = (mode == 2) ? 1 : 0;
     e = launch_combine(kc, s);
     if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
     ctx->launches += 1;
@@ -572,6 +578,39 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
+}
+
+int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                const uint8_t *in, size_t len, uint8_t *out, void *stream)
+{
+    static const uint8_t no_tag[1] = {0};
+    int rc = check_common(ctx, key, key_len, iv, iv_len, nullptr, 0, in, len, out, no_tag, GCM_MEM_DEVICE);
+    if (rc) return rc;
+    if (len == 0) return GCM_OK;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch sc;
+    rc = enqueue_device(ctx, key, key_len, iv, iv_len, nullptr, 0, in, len, out, nullptr, false, nullptr, sc, s, 1);
+    if (sc.base) scratch_free(ctx, sc, s);
+    return rc;
+}
+
+int gcm_ghash(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *aad, size_t aad_len,
+              const uint8_t *data, size_t len, uint8_t *out16, void *stream)
+{
+    static const uint8_t iv96[12] = {0};  // H does not depend on the IV; J0 is unused
+    int rc = check_common(ctx, key, key_len, iv96, sizeof(iv96), aad, aad_len, data, len, data, out16,
+                          GCM_MEM_DEVICE);
+    if (rc) return rc;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch sc;
+    rc = enqueue_device(ctx, key, key_len, iv96, sizeof(iv96), aad, aad_len, data, len, nullptr, out16, false,
+                        nullptr, sc, s, 2);
+    if (sc.base) scratch_free(ctx, sc, s);
+    return rc;
 }
 
 int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,

@@ -135,6 +135,7 @@ struct KcParams {
     uint8_t *tag_out;       // 16 bytes (device), may be null
     const uint8_t *tag_expected;  // 16 bytes (device) for decrypt, else null
     int32_t *status;        // device status word (decrypt), may be null
+    int raw;                // 1: output GHASH_H(A, C) itself (no E_K(J0) mask)
 };
 
 struct KzParams {
@@ -146,7 +147,8 @@ struct KzParams {
 // Launchers (defined in gcm_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream);
 cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
-cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream);
+// mode: 0 full GCM, 1 CTR keystream only, 2 GHASH only (no AES, no output)
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode = 0);
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
 cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,

@@ -369,6 +369,12 @@ __device__ __forceinline__ uint4 keep_bytes(const uint4 &v, uint32_t nbytes)
     return make_uint4(m[0], m[1], m[2], m[3]);
 }
 
+// What a fused pass computes: full GCM (CTR keystream + GHASH), the CTR
+// keystream XOR alone, or GHASH alone over the input (no AES, no output).
+constexpr int MODE_GCM = 0;
+constexpr int MODE_CTR = 1;
+constexpr int MODE_GHASH = 2;
+
 // Everything a tile needs to know about its message.
 struct MsgView {
     const uint8_t *in;
@@ -462,7 +468,7 @@ struct GroupCache {
 // reduces the 16 warp partials into v.partials[tile].
 // Needs the round tables, the message's GHASH table and segment factors in
 // shared memory; contains two __syncthreads.
-template <int NR>
+template <int NR, int MODE = MODE_GCM>
 __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const MsgConst &c, const uint32_t *rk,
                                           const LaneConst &L, uint64_t tile, GroupCache &gc)
 {
@@ -513,6 +519,16 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 // (small) offset in the next window.
                 const uint32_t dn = d + 32u;
                 if (dn < seg_len) din_next = __ldcs(in + dn);
+                if (MODE == MODE_GHASH) {
+                    if (active) {
+                        uint4 m = ghash_mul_table(smem, acc, L);
+                        xor4(m, din);
+                        acc = m;
+                        dlast = d;
+                        have = true;
+                    }
+                    continue;
+                }
                 if ((W >> 8) != gc.grp) {
                     // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
                     gc.grp = W >> 8;
@@ -534,11 +550,13 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 if (active) {
                     ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
                     __stcs(out + d, ks);
-                    uint4 m = ghash_mul_table(smem, acc, L);
-                    xor4(m, v.dec ? din : ks);
-                    acc = m;
-                    dlast = d;
-                    have = true;
+                    if (MODE == MODE_GCM) {
+                        uint4 m = ghash_mul_table(smem, acc, L);
+                        xor4(m, v.dec ? din : ks);
+                        acc = m;
+                        dlast = d;
+                        have = true;
+                    }
                 }
             }
         } else {
@@ -557,6 +575,10 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                         x = *reinterpret_cast<const uint4 *>(src);
                     else
                         x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
+                } else if (MODE == MODE_GHASH) {
+                    const uint64_t j = s - v.a_blocks;
+                    x = (j < v.n_full) ? __ldcs(reinterpret_cast<const uint4 *>(v.in) + j)
+                                       : load_partial(v.in + j * 16u, (uint32_t)(v.len - j * 16u));
                 } else {
                     const uint64_t j = s - v.a_blocks;
                     const uint32_t ctr = c.ctr0 + 1u + (uint32_t)j;
@@ -579,14 +601,17 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                         x = v.dec ? din : cb;
                     }
                 }
-                uint4 m = ghash_mul_table(smem, acc, L);
-                xor4(m, x);
-                acc = m;
-                dlast = q;
-                have = true;
+                if (MODE != MODE_CTR) {
+                    uint4 m = ghash_mul_table(smem, acc, L);
+                    xor4(m, x);
+                    acc = m;
+                    dlast = q;
+                    have = true;
+                }
             }
         }
     }
+    if (MODE == MODE_CTR) return;  // no authenticator: nothing to reduce
 
     // Close the lane's chain (its last block is e = seg_len - dlast blocks
     // before the segment end, 1 <= e <= 32), reduce the warp, move the
@@ -611,7 +636,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
 }
 
 // KF: one message, tiles [tile_begin, tile_end) over a persistent grid.
-template <int NR>
+template <int NR, int MODE = MODE_GCM>
 __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -645,7 +670,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
     gc.grp = 0xFFFFFFFFu;
     gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
     for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
-        tile_body<NR>(smem, v, c, rk, L, tile, gc);
+        tile_body<NR, MODE>(smem, v, c, rk, L, tile, gc);
 }
 
 // ---------------------------------------------------------------------
@@ -929,8 +954,9 @@ __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ K
         lb.w[3] = (uint32_t)cbits;
         const gf128 gh = gf_mul(gf_xor(s, lb), km->H);
         const uint4 gm = gf_to_mem(gh);
-        const uint32_t tw[4] = {gm.x ^ p.mm->ej0[0], gm.y ^ p.mm->ej0[1], gm.z ^ p.mm->ej0[2],
-                                gm.w ^ p.mm->ej0[3]};
+        const uint32_t mask[4] = {p.raw ? 0u : p.mm->ej0[0], p.raw ? 0u : p.mm->ej0[1], p.raw ? 0u : p.mm->ej0[2],
+                                  p.raw ? 0u : p.mm->ej0[3]};
+        const uint32_t tw[4] = {gm.x ^ mask[0], gm.y ^ mask[1], gm.z ^ mask[2], gm.w ^ mask[3]};
         uint8_t tag[16];
         for (int b = 0; b < 16; b++) tag[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
         if (p.tag_out)
@@ -997,11 +1023,18 @@ cudaError_t configure_kernels()
     cudaError_t e;
     e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fused_kernel<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+#define SET_SMEM(K)                                                                         \
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES); \
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(fused_kernel<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(fused_kernel<14>, cudaFuncAttributeMaxDynamicSharedMemorySize, KF_SMEM_BYTES);
+    SET_SMEM((fused_kernel<10, MODE_GCM>));
+    SET_SMEM((fused_kernel<12, MODE_GCM>));
+    SET_SMEM((fused_kernel<14, MODE_GCM>));
+    SET_SMEM((fused_kernel<10, MODE_CTR>));
+    SET_SMEM((fused_kernel<12, MODE_CTR>));
+    SET_SMEM((fused_kernel<14, MODE_CTR>));
+    SET_SMEM((fused_kernel<14, MODE_GHASH>));
+#undef SET_SMEM
+    return cudaSuccess;
 }
 
 cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream)
@@ -1016,13 +1049,27 @@ cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream)
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode)
 {
     if (p.tile_end <= p.tile_begin) return cudaSuccess;
+    if (mode == MODE_GHASH) {
+        fused_kernel<14, MODE_GHASH><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        return cudaGetLastError();
+    }
+    const bool ctr = (mode == MODE_CTR);
     switch (nr) {
-    case 10: fused_kernel<10><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
-    case 12: fused_kernel<12><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
-    case 14: fused_kernel<14><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); break;
+    case 10:
+        if (ctr) fused_kernel<10, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        else fused_kernel<10, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        break;
+    case 12:
+        if (ctr) fused_kernel<12, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        else fused_kernel<12, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        break;
+    case 14:
+        if (ctr) fused_kernel<14, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        else fused_kernel<14, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
