@@ -905,6 +905,148 @@ def run_catalog(args):
     return 0
 
 
+def run_small(args):
+    """The plain single-message workload: one 1 MiB AES-128-GCM message
+    (uniform random bytes, 96-bit IV, 20-byte AAD), encrypt then
+    decrypt-verify through gcm_encrypt / gcm_decrypt_verify on device
+    buffers.  The timed steps rotate over 256 distinct messages (256 MiB of
+    inputs, above the 129 MB L2), so no step reads a warm input; message 0 is
+    the seeded message the parity tests use and is checked against the oracle
+    first."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2602_23067_gb300 import Context, _native, workloads
+
+    rank, local, world = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    n_msgs, size = 256, 1 << 20
+    r = workloads.rng(1)
+    key = r.integers(0, 256, 16, dtype=np.uint8).tobytes()
+    iv = r.integers(0, 256, 12, dtype=np.uint8).tobytes()
+    aad = r.integers(0, 256, 20, dtype=np.uint8).tobytes()
+    pt0 = workloads.random_bytes(11, size).tobytes()
+    ctx = Context(local)
+    stream = torch.cuda.current_stream()
+    pts = torch.empty((n_msgs, size), dtype=torch.uint8, device="cuda")
+    pts[0].copy_(torch.frombuffer(bytearray(pt0), dtype=torch.uint8))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1 + rank)
+    pts[1:].random_(0, 256, generator=g)
+    cts = torch.empty_like(pts)
+    backs = torch.empty_like(pts)
+    tags = torch.empty((n_msgs, 16), dtype=torch.uint8, device="cuda")
+    d_aad = torch.frombuffer(bytearray(aad), dtype=torch.uint8).cuda()
+
+    def step(i):
+        ctx.encrypt_device(key, iv, d_aad, pts[i], ct=cts[i], tag=tags[i], stream=stream)
+        ctx.decrypt_verify_device(key, iv, d_aad, cts[i], tags[i], pt=backs[i], stream=stream)
+
+    step(0)
+    torch.cuda.synchronize()
+    ref_ct, ref_tag = oracle.gcm_encrypt(key, iv, aad, pt0)
+    if bytes(tags[0].cpu().numpy()) != ref_tag or bytes(cts[0].cpu().numpy()) != ref_ct:
+        raise SystemExit("1 MiB message differs from the oracle")
+    if not torch.equal(backs[0], pts[0]):
+        raise SystemExit("1 MiB round trip mismatch")
+    for i in range(max(args.warmup, 3)):
+        step(i % n_msgs)
+    steps = max(args.steps, 200)
+    _native.gcm_profile_enable(ctx.handle, True)
+    _native.gcm_profile_read(ctx.handle, reset=True)
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.25)
+    torch.cuda.synchronize()
+    lat = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        t0 = time.perf_counter()
+        step(k % n_msgs)  # decrypt-verify returns after the verdict is on the host
+        lat.append(time.perf_counter() - t0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = _native.gcm_profile_read(ctx.handle, reset=True)
+    _native.gcm_profile_enable(ctx.handle, False)
+
+    # the allocation-free entry point, encryption only, same rotation
+    tagbuf = torch.empty(16, dtype=torch.uint8, device="cuda")
+    kb, ib = (ctypes_buf(key), ctypes_buf(iv))
+    na_lat = []
+    for k in range(steps + 3):
+        i = k % n_msgs
+        t0 = time.perf_counter()
+        rc = _native.gcm_encrypt_noalloc(kb[0], len(key), ib[0], len(iv), d_aad.data_ptr(), len(aad),
+                                         pts[i].data_ptr(), size, cts[i].data_ptr(), tagbuf.data_ptr(),
+                                         stream.cuda_stream)
+        if rc:
+            raise SystemExit("gcm_encrypt_noalloc failed: %s" % _native.noalloc_last_error())
+        stream.synchronize()
+        if k >= 3:
+            na_lat.append(time.perf_counter() - t0)
+    if rank != 0:
+        return 0
+    peak, peak_kind = load_peaks()
+    kern_ms = prof["fused_ms"] / max(1, prof["fused_launches"])
+    kern_bytes = prof["fused_bytes"] / max(1, prof["fused_launches"])
+    achieved = kern_bytes / (kern_ms * 1e-3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        c, t = oracle.gcm_encrypt(key, iv, aad, pt0)
+        ok, _ = oracle.gcm_decrypt(key, iv, aad, c, t)
+        dt = time.perf_counter() - t0
+        assert ok
+        cpu = {"value": 2 * size / dt / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": "the whole 1 MiB message 0, encrypt + decrypt-verify, one host thread (%.2f s)" % dt}
+    us = [x * 1e6 for x in lat]
+    line = {
+        "metric": "AES-128-GCM GB/s, one 1 MiB message per call (encrypt + decrypt-verify), latency p50/p99",
+        "value": world * 2 * size * steps / (ms * 1e-3) / 1e9,
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": ms / steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "plain_1MiB_aes128gcm_enc+dec", "cipher": "AES-128-GCM", "iv_bits": 96,
+                   "aad_bytes": 20, "payload_bytes": size,
+                   "l2": "steps rotate over 256 distinct 1 MiB messages (256 MiB > 129 MB L2)"},
+        "latency_us": {"p50": percentile(us, 0.5), "p99": percentile(us, 0.99), "mean": statistics.mean(us),
+                       "what": "host wall time of gcm_encrypt + gcm_decrypt_verify (the verdict read back)"},
+        "noalloc_encrypt_latency_us": {"p50": percentile([x * 1e6 for x in na_lat], 0.5),
+                                       "p99": percentile([x * 1e6 for x in na_lat], 0.99),
+                                       "what": "gcm_encrypt_noalloc + stream synchronize"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "fused_kernel<10> (AES-128 CTR + GHASH map)",
+                     "algorithmic_bytes_per_launch": kern_bytes, "avg_launch_ms": kern_ms,
+                     "peak_source": "%s hbm_gbs" % peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": None,
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def ctypes_buf(b: bytes):
+    import ctypes
+
+    buf = ctypes.create_string_buffer(b, len(b))
+    return ctypes.addressof(buf), buf
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -915,7 +1057,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-bytes", type=int, default=8 << 20)
     ap.add_argument("--catalog-pairs", type=int, default=683, help="catalog: float32/int16 file pairs (683 = 64 GiB)")
-    ap.add_argument("--workload", choices=["fits4g", "batched", "serving", "catalog"], default="fits4g",
+    ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog"], default="fits4g",
                     help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages; "
                          "serving: Poisson request stream")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving arrival rates (req/s)")
@@ -933,6 +1075,8 @@ def main():
         raise SystemExit("--warmup must be at least 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "small":
+        return run_small(args)
     if args.workload == "batched":
         return run_batched(args)
     if args.workload == "serving":

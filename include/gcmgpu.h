@@ -109,6 +109,14 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                        const uint8_t *ct, size_t len, const uint8_t *tag,
                        uint8_t *pt, int mem, void *stream);
 
+/* Waits until everything enqueued on `stream` (a cudaStream_t; NULL is the
+ * legacy default stream) has finished on the context's device, and reports
+ * an asynchronous CUDA error from that work as GCM_ERR_CUDA.  The
+ * asynchronous device-mode calls (gcm_encrypt, gcm_ctr_xor, gcm_ghash) need
+ * it, or any other synchronisation of the stream, before their outputs are
+ * read on the host. */
+int gcm_sync(gcm_ctx *ctx, void *stream);
+
 /* ---------------------------------------------------------------- */
 /* The two halves of the fused pass on their own                    */
 /* ---------------------------------------------------------------- */

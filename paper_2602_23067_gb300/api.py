@@ -141,6 +141,11 @@ class Context:
                                  _stream_handle(stream)))
         return pt
 
+    def sync(self, stream=None) -> None:
+        """gcm_sync: wait for the work enqueued on `stream` (default: torch's
+        current stream) and raise GcmError on an asynchronous CUDA error."""
+        check(lib.gcm_sync(self.handle, _stream_handle(stream)))
+
     def ctr_xor_device(self, key: bytes, iv: bytes, inp, out=None, stream=None):
         """Enqueue the CTR keystream XOR alone (gcm_ctr_xor); returns out."""
         import torch

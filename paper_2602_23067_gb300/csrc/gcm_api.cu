@@ -580,6 +580,16 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
     delete ctx;
 }
 
+int gcm_sync(gcm_ctx *ctx, void *stream)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronisation");
+    return GCM_OK;
+}
+
 int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
                 const uint8_t *in, size_t len, uint8_t *out, void *stream)
 {

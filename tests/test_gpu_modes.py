@@ -58,7 +58,7 @@ def test_ctr_alone_is_the_gcm_ciphertext(env, key_len):
         ref_ct, _ = oracle.gcm_encrypt(key, iv, b"", pt)
         x = dev(torch, pt)
         y = ctx.ctr_xor_device(key, iv, x)
-        torch.cuda.synchronize()
+        ctx.sync()  # gcm_sync on torch's current stream
         assert bytes(y.cpu().numpy()) == ref_ct, n
         # involution, in place
         ctx.ctr_xor_device(key, iv, y, out=y)
