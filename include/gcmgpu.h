@@ -109,6 +109,19 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                        const uint8_t *ct, size_t len, const uint8_t *tag,
                        uint8_t *pt, int mem, void *stream);
 
+/* Sets how many keys the session keeps set up on the device for
+ * gcm_encrypt / gcm_decrypt_verify / gcm_ctr_xor / gcm_ghash (default 64;
+ * 0 disables the cache).  A call whose key is cached skips the key setup
+ * (round keys, H and its power tables, about 67 KB per key) and only derives
+ * J0 and E_K(J0) for its IV; a new key replaces the least recently used entry
+ * that no call in flight still reads.  The cache holds key material on the
+ * device and the key bytes in host memory until the entry is replaced, the
+ * cache is shrunk, or the context is destroyed (the bytes are zeroed then).
+ * Shrinking waits for the cached entries' last uses; it returns
+ * GCM_ERR_BUSY if another thread's call holds an entry at that moment.  No
+ * counterpart in the paper, which sets up the key per call. */
+int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
+
 /* Waits until everything enqueued on `stream` (a cudaStream_t; NULL is the
  * legacy default stream) has finished on the context's device, and reports
  * an asynchronous CUDA error from that work as GCM_ERR_CUDA.  The

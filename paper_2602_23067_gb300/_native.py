@@ -88,6 +88,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_encrypt_noalloc": (ctypes.c_int, [_VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP]),
     "gcm_sync": (ctypes.c_int, [_VP, _VP]),
+    "gcm_ctx_set_key_cache": (ctypes.c_int, [_VP, _SZ]),
     "gcm_ctr_xor": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP]),
     "gcm_ghash": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP]),
     "gfc_fits_layout": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(GfcLayout)]),

@@ -141,6 +141,10 @@ class Context:
                                  _stream_handle(stream)))
         return pt
 
+    def set_key_cache(self, entries: int) -> None:
+        """gcm_ctx_set_key_cache: keys kept set up on the device (0 = off)."""
+        check(lib.gcm_ctx_set_key_cache(self.handle, entries))
+
     def sync(self, stream=None) -> None:
         """gcm_sync: wait for the work enqueued on `stream` (default: torch's
         current stream) and raise GcmError on an asynchronous CUDA error."""

@@ -79,7 +79,7 @@ cudaEvent_t take_event(gcm_ctx *ctx)
 uint32_t tile_log2_for(uint64_t M, int num_sms)
 {
     uint32_t lg = 16;
-    while (lg > 10 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
+    while (lg > (uint32_t)SEGF_MIN_LOG2 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
     return lg;
 }
 
@@ -137,6 +137,93 @@ int check_common(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t
     return GCM_OK;
 }
 
+// The context's key-material cache.  key_cache_acquire returns the slot of
+// `ks.key` with ks.km pointing at its device key material and this
+// message's J0 / E_K(J0) setup already enqueued on s: the full key setup
+// when the key is new to the cache, only the message part when it is cached
+// (after waiting for the stream that set it up).  It returns -1 when the key
+// cannot be cached now (cache disabled or every entry in use); the caller
+// then sets up private key material.  A held slot is released, after the
+// call's last kernel that reads it, by key_cache_release.
+int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &err)
+{
+    err = cudaSuccess;
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->key_cache_cap == 0) return -1;
+    auto &C = ctx->key_cache;
+    int slot = -1;
+    for (size_t i = 0; i < C.size(); i++)
+        if (C[i].key_len == ks.key_len && memcmp(C[i].key, ks.key, ks.key_len) == 0) {
+            slot = (int)i;
+            break;
+        }
+    bool fresh = false;
+    if (slot < 0) {
+        if (C.size() < ctx->key_cache_cap) {
+            gcm_ctx::KeyCacheEntry e;
+            if (cudaMalloc(reinterpret_cast<void **>(&e.km), sizeof(KeyMat)) != cudaSuccess) {
+                cudaGetLastError();
+                return -1;
+            }
+            if (cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming) != cudaSuccess) {
+                cudaFree(e.km);
+                cudaGetLastError();
+                return -1;
+            }
+            C.push_back(e);
+            slot = (int)C.size() - 1;
+        } else {
+            // Least recently used entry that no call holds and whose last
+            // use has completed on every stream.
+            uint64_t best = UINT64_MAX;
+            for (size_t i = 0; i < C.size(); i++) {
+                if (C[i].holders || C[i].tick >= best) continue;
+                bool idle = cudaEventQuery(C[i].ready) == cudaSuccess;
+                for (auto &u : C[i].uses) idle = idle && cudaEventQuery(u.second) == cudaSuccess;
+                if (idle) {
+                    best = C[i].tick;
+                    slot = (int)i;
+                }
+            }
+            cudaGetLastError();  // clears cudaErrorNotReady left by the queries
+            if (slot < 0) return -1;
+        }
+        fresh = true;
+    }
+    auto &e = C[slot];
+    ks.km = e.km;
+    if (fresh) {
+        memcpy(e.key, ks.key, ks.key_len);
+        e.key_len = ks.key_len;
+        err = launch_key_setup(ks, s);
+        if (err == cudaSuccess) err = cudaEventRecord(e.ready, s);
+        if (err != cudaSuccess) {
+            memset(e.key, 0, sizeof(e.key));
+            e.key_len = 0;
+            return -1;
+        }
+    } else {
+        err = cudaStreamWaitEvent(s, e.ready, 0);
+        if (err == cudaSuccess) err = launch_msg_only(ks, s);
+        if (err != cudaSuccess) return -1;
+    }
+    e.tick = ++ctx->key_cache_tick;
+    e.holders++;
+    return slot;
+}
+
+void key_cache_release(gcm_ctx *ctx, int slot, cudaStream_t s)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto &e = ctx->key_cache[slot];
+    cudaEvent_t ev = nullptr;
+    for (auto &u : e.uses)
+        if (u.first == s) ev = u.second;
+    if (!ev && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess) e.uses.push_back({s, ev});
+    if (ev) cudaEventRecord(ev, s);
+    e.holders--;
+}
+
 // Enqueues the whole device path for one message whose aad/in/out/tag live
 // in device memory.  For decryption `tag_dev` is the expected tag and
 // `status_dev` receives 0 or GCM_ERR_AUTH; for encryption the tag is written.
@@ -184,12 +271,30 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         if (e != cudaSuccess) return cuda_fail(e, "IV copy");
         ks.iv_dev = div;
     }
-    ks.km = km;
     ks.mm = mm;
     ks.tabs = ctx->tabs;
-    cudaError_t e = launch_key_setup(ks, s);
+    cudaError_t e = cudaSuccess;
+    const int slot = key_cache_acquire(ctx, ks, s, e);
     if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
+    if (slot >= 0) {
+        km = ks.km;
+    } else {
+        ks.km = km;
+        e = launch_key_setup(ks, s);
+        if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
+    }
     ctx->launches += 1;
+    // Releases the cache slot after the last kernel of this call that reads
+    // the key material has been enqueued (on every return path below).
+    struct SlotGuard {
+        gcm_ctx *ctx;
+        int slot;
+        cudaStream_t s;
+        ~SlotGuard()
+        {
+            if (slot >= 0) key_cache_release(ctx, slot, s);
+        }
+    } slot_guard{ctx, slot, s};
 
     const int nr = (int)key_len / 4 + 6;
     KfParams kf;
@@ -574,10 +679,40 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
         for (auto e : ctx->spare) cudaEventDestroy(e);
         stream_release(ctx);
         for (auto k : ctx->keys) cudaFree(k);
+        for (auto &c : ctx->key_cache) {
+            memset(c.key, 0, sizeof(c.key));
+            cudaFree(c.km);
+            cudaEventDestroy(c.ready);
+            for (auto &u : c.uses) cudaEventDestroy(u.second);
+        }
+        ctx->key_cache.clear();
         if (ctx->tabs) cudaFree(ctx->tabs);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
+}
+
+int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (entries > 4096) return fail(GCM_ERR_INVALID_ARG, "at most 4096 cached keys");
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (entries < ctx->key_cache.size()) {
+        for (auto &c : ctx->key_cache)
+            if (c.holders) return fail(GCM_ERR_BUSY, "cached keys are in use by calls in flight");
+        DeviceGuard guard(ctx->device);
+        for (auto &c : ctx->key_cache) {
+            cudaEventSynchronize(c.ready);
+            for (auto &u : c.uses) cudaEventSynchronize(u.second);
+            memset(c.key, 0, sizeof(c.key));
+            cudaFree(c.km);
+            cudaEventDestroy(c.ready);
+            for (auto &u : c.uses) cudaEventDestroy(u.second);
+        }
+        ctx->key_cache.clear();
+    }
+    ctx->key_cache_cap = entries;
+    return GCM_OK;
 }
 
 int gcm_sync(gcm_ctx *ctx, void *stream)

@@ -48,6 +48,22 @@ struct gcm_ctx {
     // registered keys (gcm_key_register)
     std::vector<gcmgpu::KeyMat *> keys;
     std::vector<uint32_t> key_nr;
+    // Key material of the single-message calls, cached per key on the device
+    // (least recently used entry replaced; guarded by mu).  An entry is only
+    // overwritten when no call holds it and every stream that used it has
+    // passed its last use.
+    struct KeyCacheEntry {
+        uint8_t key[32];
+        uint32_t key_len = 0;
+        gcmgpu::KeyMat *km = nullptr;
+        uint64_t tick = 0;            // last use, for LRU
+        int holders = 0;              // calls between acquire and release
+        cudaEvent_t ready = nullptr;  // recorded after the entry's key setup
+        std::vector<std::pair<cudaStream_t, cudaEvent_t>> uses;  // last use per stream
+    };
+    std::vector<KeyCacheEntry> key_cache;
+    size_t key_cache_cap = 64;
+    uint64_t key_cache_tick = 0;
 };
 
 namespace gcmgpu {

@@ -72,26 +72,97 @@ __device__ __forceinline__ gf128 gf_mul_x(const gf128 &v)
     return r;
 }
 
-// General product a * b: shift-and-add over the 128 coefficients of a,
-// lowest power first.  Used for the rare multiplications (key setup, the
-// per-thread and per-tile combine); the per-block multiplications of the hot
-// loop go through the shared-memory table instead.
-static __device__ __noinline__ gf128 gf_mul(gf128 a, gf128 b)
+// ---------------------------------------------------------------------
+// General product a * b (the rare multiplications: key setup, the closing of
+// a lane's chain, segment factors, the tree combine).  The per-block
+// multiplications of the hot loop go through the shared-memory table.
+//
+// Carry-less multiplication from integer multiplication: split a 32-bit
+// operand into four "sparse" parts holding only the bits at positions
+// = i (mod 4).  In the integer product of two sparse parts every position of
+// one residue class receives the count of bit pairs that land there (at most
+// 8), which needs 4 bits, so the counts of neighbouring positions of the class
+// (4 apart) never overlap and no carry reaches another position of the class:
+// the bit at each such position is the count mod 2, i.e. the carry-less
+// product.  XOR of the four products per class and a mask per class give the
+// 64-bit carry-less product.  Two levels of Karatsuba build the 128 x 128
+// product from nine such multiplies; the 255-bit product is then reduced
+// modulo x^128 + x^7 + x^2 + x + 1.  Everything is data-independent (no
+// branches, no table), so the latency is a few hundred cycles instead of the
+// 128 dependent steps of shift-and-add.
+// ---------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint32_t brev32(uint32_t x)
 {
-    gf128 z = gf_zero();
-    gf128 v = b;
-#pragma unroll 1
-    for (int wi = 0; wi < 4; wi++) {
-        uint32_t aw = a.w[wi];
-#pragma unroll 8
-        for (int bit = 0; bit < 32; bit++) {
-            uint32_t m = (uint32_t)((int32_t)(aw << bit) >> 31);
-#pragma unroll
-            for (int k = 0; k < 4; k++) z.w[k] ^= v.w[k] & m;
-            v = gf_mul_x(v);
-        }
-    }
-    return z;
+#ifdef __CUDA_ARCH__
+    return __brev(x);
+#else
+    uint32_t r = 0u;
+    for (int i = 0; i < 32; i++) r |= ((x >> i) & 1u) << (31 - i);
+    return r;
+#endif
+}
+
+// 32 x 32 -> 64-bit carry-less product; bit i of x is the coefficient of t^i.
+__host__ __device__ __forceinline__ uint64_t clmul32(uint32_t x, uint32_t y)
+{
+    const uint32_t x0 = x & 0x11111111u, x1 = x & 0x22222222u, x2 = x & 0x44444444u, x3 = x & 0x88888888u;
+    const uint32_t y0 = y & 0x11111111u, y1 = y & 0x22222222u, y2 = y & 0x44444444u, y3 = y & 0x88888888u;
+    const uint64_t z0 = ((uint64_t)x0 * y0) ^ ((uint64_t)x1 * y3) ^ ((uint64_t)x2 * y2) ^ ((uint64_t)x3 * y1);
+    const uint64_t z1 = ((uint64_t)x0 * y1) ^ ((uint64_t)x1 * y0) ^ ((uint64_t)x2 * y3) ^ ((uint64_t)x3 * y2);
+    const uint64_t z2 = ((uint64_t)x0 * y2) ^ ((uint64_t)x1 * y1) ^ ((uint64_t)x2 * y0) ^ ((uint64_t)x3 * y3);
+    const uint64_t z3 = ((uint64_t)x0 * y3) ^ ((uint64_t)x1 * y2) ^ ((uint64_t)x2 * y1) ^ ((uint64_t)x3 * y0);
+    return (z0 & 0x1111111111111111ull) | (z1 & 0x2222222222222222ull) | (z2 & 0x4444444444444444ull) |
+           (z3 & 0x8888888888888888ull);
+}
+
+// 64 x 64 -> 128-bit carry-less product (one Karatsuba level).
+__host__ __device__ __forceinline__ void clmul64(uint64_t a, uint64_t b, uint64_t &lo, uint64_t &hi)
+{
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    const uint64_t p0 = clmul32(a0, b0), p2 = clmul32(a1, b1);
+    const uint64_t p1 = clmul32(a0 ^ a1, b0 ^ b1) ^ p0 ^ p2;
+    lo = p0 ^ (p1 << 32);
+    hi = p2 ^ (p1 >> 32);
+}
+
+// Product of two field elements given as poly words (see the top of this
+// file): out = a * b mod x^128 + x^7 + x^2 + x + 1.
+__host__ __device__ __forceinline__ void gf_mul_words(const uint32_t a[4], const uint32_t b[4], uint32_t out[4])
+{
+    // Bit-reversing each poly word puts the coefficient of x^i at bit i of
+    // the 128-bit little-endian integer (A0 = x^0..x^63, A1 = x^64..x^127).
+    const uint64_t A0 = (uint64_t)brev32(a[0]) | ((uint64_t)brev32(a[1]) << 32);
+    const uint64_t A1 = (uint64_t)brev32(a[2]) | ((uint64_t)brev32(a[3]) << 32);
+    const uint64_t B0 = (uint64_t)brev32(b[0]) | ((uint64_t)brev32(b[1]) << 32);
+    const uint64_t B1 = (uint64_t)brev32(b[2]) | ((uint64_t)brev32(b[3]) << 32);
+    uint64_t l0, h0, l2, h2, l1, h1;
+    clmul64(A0, B0, l0, h0);
+    clmul64(A1, B1, l2, h2);
+    clmul64(A0 ^ A1, B0 ^ B1, l1, h1);
+    l1 ^= l0 ^ l2;
+    h1 ^= h0 ^ h2;
+    // 255-bit product P3:P2:P1:P0 (64-bit words, P3 < 2^63).
+    const uint64_t P0 = l0, P1 = h0 ^ l1, P2 = l2 ^ h1, P3 = h2;
+    // x^128 = x^7 + x^2 + x + 1: the high half Q = P3:P2 folds back as
+    // Q * (1 + x + x^2 + x^7).  Its bits pushed above x^127 (the top 7 bits
+    // of Q shifted by 1, 2, 7) fold once more; adding them into the low bits
+    // of Q first (T) makes one pass of shifts do both folds.
+    const uint64_t T0 = P2 ^ (P3 >> 63) ^ (P3 >> 62) ^ (P3 >> 57);
+    const uint64_t T1 = P3;
+    const uint64_t R0 = T0 ^ (T0 << 1) ^ (T0 << 2) ^ (T0 << 7);
+    const uint64_t R1 = T1 ^ ((T1 << 1) | (T0 >> 63)) ^ ((T1 << 2) | (T0 >> 62)) ^ ((T1 << 7) | (T0 >> 57));
+    const uint64_t Z0 = P0 ^ R0, Z1 = P1 ^ R1;
+    out[0] = brev32((uint32_t)Z0);
+    out[1] = brev32((uint32_t)(Z0 >> 32));
+    out[2] = brev32((uint32_t)Z1);
+    out[3] = brev32((uint32_t)(Z1 >> 32));
+}
+
+__device__ __forceinline__ gf128 gf_mul(const gf128 &a, const gf128 &b)
+{
+    gf128 r;
+    gf_mul_words(a.w, b.w, r.w);
+    return r;
 }
 
 // Spreads the 16 bits of x so that bit q lands on bit 2q (zeros between).

@@ -17,6 +17,8 @@ constexpr int KF_WARPS = KF_THREADS / 32;
 constexpr int KF_LOG2_WARPS = 4;
 constexpr int GH_STRIDE = 32;
 constexpr int GH_LOG2_STRIDE = 5;
+constexpr int SEGF_MIN_LOG2 = 9;   // smallest tile: 2^9 blocks (32 per warp)
+constexpr int SEGF_SIZES = 8;      // tile sizes 2^9 .. 2^16
 constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
 constexpr uint32_t BATCH_TILE_LOG2 = 16;  // tile size of the batched kernel (2^16 blocks)
 constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
@@ -37,7 +39,8 @@ struct KeyMat {
     gf128 H;                    // hash subkey E_K(0^128), poly words
     gf128 h2k[H2K_COUNT];       // H^(2^k): the stride table of the tree (Sec. 3.3.1)
     gf128 hpow[GH_STRIDE];      // H^1 .. H^32: per-lane closing factors
-    gf128 segf16[KF_WARPS];     // H^((15-w) * 2^12): warp factors for 2^16-block tiles
+    gf128 segf[SEGF_SIZES][KF_WARPS];  // [lg - SEGF_MIN_LOG2][w] = H^((15-w) * 2^(lg-4)): warp
+                                        // factors for tiles of 2^lg blocks, lg = 9..16
     uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^32, memory words
 };
 
@@ -147,6 +150,8 @@ struct KzParams {
 // Launchers (defined in gcm_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream);
 cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
+// J0 and E_K(J0) only, into p.mm, for key material p.km set up earlier.
+cudaError_t launch_msg_only(const KsParams &p, cudaStream_t stream);
 // mode: 0 full GCM, 1 CTR keystream only, 2 GHASH only (no AES, no output)
 cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode = 0);
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);

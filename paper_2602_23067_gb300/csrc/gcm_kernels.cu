@@ -193,15 +193,17 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         }
         km->hpow[e - 1] = acc;
     }
-    if (t >= 64 && t < 64 + KF_WARPS) {
-        // H^((15-w) * 2^12) for 2^16-block tiles (the batched kernel's size).
-        const int w = t - 64, steps = KF_WARPS - 1 - w;
+    if (t >= 128 && t < 128 + SEGF_SIZES * KF_WARPS) {
+        // H^((15-w) * 2^(lg-4)) for every tile size 2^lg the kernels use.
+        const int w = (t - 128) & (KF_WARPS - 1), sz = (t - 128) / KF_WARPS;
+        const int steps = KF_WARPS - 1 - w;
+        const int base = SEGF_MIN_LOG2 + sz - KF_LOG2_WARPS;
         gf128 f;
         f.w[0] = 0x80000000u;
         f.w[1] = f.w[2] = f.w[3] = 0u;
         for (int b = 0; b < KF_LOG2_WARPS; b++)
-            if ((steps >> b) & 1) f = gf_mul(f, sh2k[BATCH_TILE_LOG2 - KF_LOG2_WARPS + b]);
-        km->segf16[w] = f;
+            if ((steps >> b) & 1) f = gf_mul(f, sh2k[base + b]);
+        km->segf[sz][w] = f;
     }
     __syncthreads();
     // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32.
@@ -433,20 +435,13 @@ __device__ __forceinline__ void stage_ghash_table(uint8_t *smem, const KeyMat *k
 }
 
 // H^((15-w) * S) for every warp w, S = 2^(tile_log2 - 4): moves a warp's
-// segment partial to the tile end.  Lane 0 of each warp writes its own.
+// segment partial to the tile end.  Lane 0 of each warp copies its own from
+// the key material.
 __device__ __forceinline__ void stage_segment_factors(uint8_t *smem, const KeyMat *km, uint32_t tile_log2)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     gf128 *segf = reinterpret_cast<gf128 *>(smem + SM_SEGF);
-    if (lane == 0) {
-        gf128 f;
-        f.w[0] = 0x80000000u;
-        f.w[1] = f.w[2] = f.w[3] = 0u;
-        const int steps = KF_WARPS - 1 - warp;
-        for (int b = 0; b < KF_LOG2_WARPS; b++)
-            if ((steps >> b) & 1) f = gf_mul(f, km->h2k[tile_log2 - KF_LOG2_WARPS + b]);
-        segf[warp] = f;
-    }
+    if (lane == 0) segf[warp] = km->segf[tile_log2 - SEGF_MIN_LOG2][warp];
 }
 
 // Per-CTA cache of the counter-group constants of AES round 2.
@@ -805,7 +800,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
             // New message: its key's GHASH table and segment factors.
             stage_ghash_table(smem, bm.km);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf16[warp];
+            if (lane == 0) reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[BATCH_TILE_LOG2 - SEGF_MIN_LOG2][warp];
             cur = mi;
             gc.grp = 0xFFFFFFFFu;
             __syncthreads();
@@ -845,35 +840,26 @@ __global__ void __launch_bounds__(256) batch_zero_kernel(const BatchMsg *msgs, u
     if (threadIdx.x < (m.len & 15)) m.out[nvec * 16 + threadIdx.x] = 0;
 }
 
-// J0 and E_K(J0) for messages whose key material is cached (one thread per
-// message; SP 800-38D Alg. 4 step 2 and the tag's E_K(J0)).
-__global__ void __launch_bounds__(128) msg_setup_kernel(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
-                                                        const DevTables *tabs)
+// J0 and E_K(J0) of one message whose key material is already set up
+// (SP 800-38D Alg. 4 step 2 and the tag's E_K(J0)); one thread.
+__device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *km, const uint8_t *sbox, MsgMat *mm)
 {
-    __shared__ uint8_t sbox[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = tabs->sbox[i];
-    __syncthreads();
-    const uint32_t mi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mi >= n) return;
-    const BatchMsg &m = msgs[mi];
-    const BatchKey &k = keys[mi];
-    const KeyMat *km = m.km;
     uint32_t j0[4];
-    if (k.iv_len == 12) {
+    if (iv_len == 12) {
         for (int i = 0; i < 3; i++)
-            j0[i] = (uint32_t)k.iv[4 * i] | ((uint32_t)k.iv[4 * i + 1] << 8) | ((uint32_t)k.iv[4 * i + 2] << 16) |
-                    ((uint32_t)k.iv[4 * i + 3] << 24);
+            j0[i] = (uint32_t)iv[4 * i] | ((uint32_t)iv[4 * i + 1] << 8) | ((uint32_t)iv[4 * i + 2] << 16) |
+                    ((uint32_t)iv[4 * i + 3] << 24);
         j0[3] = 0x01000000u;
     } else {
         const gf128 H = km->H;
         gf128 y = gf_zero();
-        for (uint32_t off = 0; off < k.iv_len; off += 16) {
+        for (uint32_t off = 0; off < iv_len; off += 16) {
             uint32_t w[4] = {0u, 0u, 0u, 0u};
-            for (uint32_t b = 0; b < 16 && off + b < k.iv_len; b++) w[b >> 2] |= (uint32_t)k.iv[off + b] << (8 * (b & 3));
+            for (uint32_t b = 0; b < 16 && off + b < iv_len; b++) w[b >> 2] |= (uint32_t)iv[off + b] << (8 * (b & 3));
             y = gf_mul(gf_xor(y, gf_from_mem(w[0], w[1], w[2], w[3])), H);
         }
         gf128 lb = gf_zero();
-        const uint64_t bits = (uint64_t)k.iv_len * 8u;
+        const uint64_t bits = (uint64_t)iv_len * 8u;
         lb.w[2] = (uint32_t)(bits >> 32);
         lb.w[3] = (uint32_t)bits;
         y = gf_mul(gf_xor(y, lb), H);
@@ -883,9 +869,32 @@ __global__ void __launch_bounds__(128) msg_setup_kernel(const BatchMsg *msgs, co
     uint32_t e[4];
     aes_block_bytes(km->rk, (int)km->nr, sbox, j0, e);
     for (int i = 0; i < 4; i++) {
-        m.mm->j0[i] = j0[i];
-        m.mm->ej0[i] = e[i];
+        mm->j0[i] = j0[i];
+        mm->ej0[i] = e[i];
     }
+}
+
+// Batched form: one thread per message.
+__global__ void __launch_bounds__(128) msg_setup_kernel(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
+                                                        const DevTables *tabs)
+{
+    __shared__ uint8_t sbox[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = tabs->sbox[i];
+    __syncthreads();
+    const uint32_t mi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (mi >= n) return;
+    msg_material(keys[mi].iv, keys[mi].iv_len, msgs[mi].km, sbox, msgs[mi].mm);
+}
+
+// Single-message form for cached key material (one warp).
+__global__ void __launch_bounds__(32) msg_only_kernel(const __grid_constant__ KsParams p)
+{
+    __shared__ uint8_t sbox[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = p.tabs->sbox[i];
+    __syncwarp();
+    if (threadIdx.x != 0) return;
+    const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
+    msg_material(iv, p.iv_len, p.km, sbox, p.mm);
 }
 
 // Key setup for many messages: one CTA each.
@@ -1040,6 +1049,12 @@ cudaError_t configure_kernels()
 cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream)
 {
     build_tables_kernel<<<1, 256, 0, stream>>>(tabs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_msg_only(const KsParams &p, cudaStream_t stream)
+{
+    msg_only_kernel<<<1, 32, 0, stream>>>(p);
     return cudaGetLastError();
 }
 

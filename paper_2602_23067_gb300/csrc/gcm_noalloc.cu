@@ -69,7 +69,7 @@ int na_cuda_fail(cudaError_t e, const char *where)
 uint32_t na_tile_log2(uint64_t M, int num_sms)
 {
     uint32_t lg = 16;
-    while (lg > 10 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
+    while (lg > (uint32_t)SEGF_MIN_LOG2 && (M >> lg) < (uint64_t)num_sms * 4) lg--;
     return lg;
 }
 
