@@ -39,38 +39,31 @@ __global__ void __launch_bounds__(256) build_tables_kernel(DevTables *tabs)
 }
 
 // ---------------------------------------------------------------------
-// Single-block AES used by the key setup (H and E_K(J0) only).
-// State: four memory words, word c = column c, byte r = row r.
+// Single-block AES for the setup kernels (H = E_K(0^128) and E_K(J0)):
+// the context's round tables T0..T3 and S-box, read through the read-only
+// cache.  State: four memory words, word c = column c, byte r = row r;
+// column c of a round takes row r from column c + r (ShiftRows).
 // ---------------------------------------------------------------------
-__device__ void aes_block_bytes(const uint32_t *rkw, int nr, const uint8_t *sbox,
-                                const uint32_t in[4], uint32_t out[4])
+__device__ void aes_block_tt(const uint32_t *rk, int nr, const DevTables *tabs, const uint32_t in[4],
+                             uint32_t out[4])
 {
-    uint32_t s[4];
-    for (int c = 0; c < 4; c++) s[c] = in[c] ^ rkw[c];
-    for (int round = 1; round <= nr; round++) {
-        uint32_t t[4];
-        for (int c = 0; c < 4; c++) {
-            // SubBytes + ShiftRows: row r of column c comes from column c + r.
-            uint32_t b0 = sbox[(s[c] >> 0) & 0xFF];
-            uint32_t b1 = sbox[(s[(c + 1) & 3] >> 8) & 0xFF];
-            uint32_t b2 = sbox[(s[(c + 2) & 3] >> 16) & 0xFF];
-            uint32_t b3 = sbox[(s[(c + 3) & 3] >> 24) & 0xFF];
-            if (round < nr) {
-                // MixColumns: row r = 2a_r ^ 3a_{r+1} ^ a_{r+2} ^ a_{r+3}.
-                uint8_t a[4] = {(uint8_t)b0, (uint8_t)b1, (uint8_t)b2, (uint8_t)b3};
-                uint8_t m[4];
-                for (int r = 0; r < 4; r++) {
-                    uint8_t x = a[r], y = a[(r + 1) & 3];
-                    m[r] = (uint8_t)(gf8_xtime(x) ^ gf8_xtime(y) ^ y ^ a[(r + 2) & 3] ^ a[(r + 3) & 3]);
-                }
-                t[c] = (uint32_t)m[0] | ((uint32_t)m[1] << 8) | ((uint32_t)m[2] << 16) | ((uint32_t)m[3] << 24);
-            } else {
-                t[c] = b0 | (b1 << 8) | (b2 << 16) | (b3 << 24);
-            }
-        }
-        for (int c = 0; c < 4; c++) s[c] = t[c] ^ rkw[4 * round + c];
+    const uint32_t *T = tabs->ttab;
+    uint32_t s0 = in[0] ^ rk[0], s1 = in[1] ^ rk[1], s2 = in[2] ^ rk[2], s3 = in[3] ^ rk[3];
+#define TT(k, w, B) __ldg(&T[(k) * 256 + (((w) >> (8 * (B))) & 0xFFu)])
+    for (int r = 1; r < nr; r++) {
+        const uint32_t n0 = TT(0, s0, 0) ^ TT(1, s1, 1) ^ TT(2, s2, 2) ^ TT(3, s3, 3) ^ rk[4 * r];
+        const uint32_t n1 = TT(0, s1, 0) ^ TT(1, s2, 1) ^ TT(2, s3, 2) ^ TT(3, s0, 3) ^ rk[4 * r + 1];
+        const uint32_t n2 = TT(0, s2, 0) ^ TT(1, s3, 1) ^ TT(2, s0, 2) ^ TT(3, s1, 3) ^ rk[4 * r + 2];
+        const uint32_t n3 = TT(0, s3, 0) ^ TT(1, s0, 1) ^ TT(2, s1, 2) ^ TT(3, s2, 3) ^ rk[4 * r + 3];
+        s0 = n0; s1 = n1; s2 = n2; s3 = n3;
     }
-    for (int c = 0; c < 4; c++) out[c] = s[c];
+#undef TT
+#define SB(w, B) ((uint32_t)__ldg(&tabs->sbox[((w) >> (8 * (B))) & 0xFFu]) << (8 * (B)))
+    out[0] = (SB(s0, 0) | SB(s1, 1) | SB(s2, 2) | SB(s3, 3)) ^ rk[4 * nr];
+    out[1] = (SB(s1, 0) | SB(s2, 1) | SB(s3, 2) | SB(s0, 3)) ^ rk[4 * nr + 1];
+    out[2] = (SB(s2, 0) | SB(s3, 1) | SB(s0, 2) | SB(s1, 3)) ^ rk[4 * nr + 2];
+    out[3] = (SB(s3, 0) | SB(s0, 1) | SB(s1, 2) | SB(s2, 3)) ^ rk[4 * nr + 3];
+#undef SB
 }
 
 // Key expansion (FIPS-197 sec. 5.2) into memory words.  Word i holds bytes
@@ -123,7 +116,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         int nr = key_expand_words(key, (int)key_len, sbox, rkw);
         s_nr = nr;
         uint32_t zero[4] = {0u, 0u, 0u, 0u}, h[4];
-        aes_block_bytes(rkw, nr, sbox, zero, h);
+        aes_block_tt(rkw, nr, tabs, zero, h);
         sH = gf_from_mem(h[0], h[1], h[2], h[3]);
     }
     __syncthreads();
@@ -163,7 +156,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
             j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
         }
         uint32_t e[4];
-        aes_block_bytes(rkw, nr, sbox, j0, e);
+        aes_block_tt(rkw, nr, tabs, j0, e);
         for (int i = 0; i < 4; i++) {
             mm->j0[i] = j0[i];
             mm->ej0[i] = e[i];
@@ -172,25 +165,22 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         km->rk[t - 64] = (t - 64 < 4 * (nr + 1)) ? rkw[t - 64] : 0u;
     }
     __syncthreads();
-    if (t == 0) {
+    // All multiplications below are branch-free selects of a factor, so the
+    // threads of a warp multiply in lockstep.
+    gf128 one;
+    one.w[0] = 0x80000000u;
+    one.w[1] = one.w[2] = one.w[3] = 0u;
+    if (t < 128) {
         // basis[i] = x^i * H^32: the 128 single-coefficient products.
-        gf128 v = sh2k[GH_LOG2_STRIDE];
-        for (int i = 0; i < 128; i++) {
-            basis[i] = v;
-            v = gf_mul_x(v);
-        }
+        gf128 xi = gf_zero();
+        xi.w[t >> 5] = 0x80000000u >> (t & 31);
+        basis[t] = gf_mul(xi, sh2k[GH_LOG2_STRIDE]);
     }
-    // H^e for e = 1..32 as a product of stride-table entries.
-    if (t >= 32 && t < 32 + GH_STRIDE) {
-        const int e = t - 31;
-        gf128 acc;
-        bool have = false;
-        for (int k = 0; k <= GH_LOG2_STRIDE; k++) {
-            if ((e >> k) & 1) {
-                acc = have ? gf_mul(acc, sh2k[k]) : sh2k[k];
-                have = true;
-            }
-        }
+    if (t < GH_STRIDE) {
+        // H^e for e = 1..32 as a product of stride-table entries.
+        const int e = t + 1;
+        gf128 acc = one;
+        for (int k = 0; k <= GH_LOG2_STRIDE; k++) acc = gf_mul(acc, ((e >> k) & 1) ? sh2k[k] : one);
         km->hpow[e - 1] = acc;
     }
     if (t >= 128 && t < 128 + SEGF_SIZES * KF_WARPS) {
@@ -198,11 +188,8 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         const int w = (t - 128) & (KF_WARPS - 1), sz = (t - 128) / KF_WARPS;
         const int steps = KF_WARPS - 1 - w;
         const int base = SEGF_MIN_LOG2 + sz - KF_LOG2_WARPS;
-        gf128 f;
-        f.w[0] = 0x80000000u;
-        f.w[1] = f.w[2] = f.w[3] = 0u;
-        for (int b = 0; b < KF_LOG2_WARPS; b++)
-            if ((steps >> b) & 1) f = gf_mul(f, sh2k[base + b]);
+        gf128 f = one;
+        for (int b = 0; b < KF_LOG2_WARPS; b++) f = gf_mul(f, ((steps >> b) & 1) ? sh2k[base + b] : one);
         km->segf[sz][w] = f;
     }
     __syncthreads();
@@ -211,8 +198,11 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
     for (int idx = t; idx < GTAB_ENTRIES; idx += blockDim.x) {
         const int v = idx >> 4, k = idx & 15;
         gf128 acc = gf_zero();
-        for (int b = 0; b < 8; b++)
-            if ((v >> b) & 1) acc = gf_xor(acc, basis[8 * k + 7 - b]);
+        for (int b = 0; b < 8; b++) {
+            const uint32_t m = 0u - (uint32_t)((v >> b) & 1);
+            const gf128 &bv = basis[8 * k + 7 - b];
+            for (int i = 0; i < 4; i++) acc.w[i] ^= bv.w[i] & m;
+        }
         km->gtab[idx] = gf_to_mem(acc);
     }
 }
@@ -842,7 +832,7 @@ __global__ void __launch_bounds__(256) batch_zero_kernel(const BatchMsg *msgs, u
 
 // J0 and E_K(J0) of one message whose key material is already set up
 // (SP 800-38D Alg. 4 step 2 and the tag's E_K(J0)); one thread.
-__device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *km, const uint8_t *sbox, MsgMat *mm)
+__device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *km, const DevTables *tabs, MsgMat *mm)
 {
     uint32_t j0[4];
     if (iv_len == 12) {
@@ -867,7 +857,7 @@ __device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *k
         j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
     }
     uint32_t e[4];
-    aes_block_bytes(km->rk, (int)km->nr, sbox, j0, e);
+    aes_block_tt(km->rk, (int)km->nr, tabs, j0, e);
     for (int i = 0; i < 4; i++) {
         mm->j0[i] = j0[i];
         mm->ej0[i] = e[i];
@@ -878,23 +868,17 @@ __device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *k
 __global__ void __launch_bounds__(128) msg_setup_kernel(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,
                                                         const DevTables *tabs)
 {
-    __shared__ uint8_t sbox[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = tabs->sbox[i];
-    __syncthreads();
     const uint32_t mi = blockIdx.x * blockDim.x + threadIdx.x;
     if (mi >= n) return;
-    msg_material(keys[mi].iv, keys[mi].iv_len, msgs[mi].km, sbox, msgs[mi].mm);
+    msg_material(keys[mi].iv, keys[mi].iv_len, msgs[mi].km, tabs, msgs[mi].mm);
 }
 
 // Single-message form for cached key material (one warp).
 __global__ void __launch_bounds__(32) msg_only_kernel(const __grid_constant__ KsParams p)
 {
-    __shared__ uint8_t sbox[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) sbox[i] = p.tabs->sbox[i];
-    __syncwarp();
     if (threadIdx.x != 0) return;
     const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
-    msg_material(iv, p.iv_len, p.km, sbox, p.mm);
+    msg_material(iv, p.iv_len, p.km, p.tabs, p.mm);
 }
 
 // Key setup for many messages: one CTA each.
@@ -921,6 +905,9 @@ __global__ void __launch_bounds__(256) batch_key_setup_kernel(const BatchMsg *ms
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ KcParams p)
 {
+    // Levels whose output fits (at most 1024 entries) run in shared memory;
+    // larger ones go through the global scratch.
+    __shared__ gf128 sbuf[2][1024];
     const int t = threadIdx.x;
     const KeyMat *km = p.km;
     uint64_t cnt = p.K;
@@ -928,12 +915,13 @@ __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ K
     // Level 0 reads the partials right to left (index g counts tiles from
     // the end of the sequence), so every right-hand operand is a full group
     // of 2^level tiles and its multiplier is exactly H^(2^(tile_log2+level)).
-    gf128 *src = p.partials;
-    gf128 *dst = p.scratch;
+    const gf128 *src = p.partials;
     bool reversed = true;
+    int flip = 0;
     while (cnt > 1) {
         const uint64_t half = (cnt + 1) / 2;
         const gf128 mult = km->h2k[p.tile_log2 + level];
+        gf128 *dst = (half <= 1024) ? sbuf[flip] : ((src == p.scratch) ? p.partials : p.scratch);
         for (uint64_t g = t; g < half; g += blockDim.x) {
             const uint64_t ri = 2 * g, li = 2 * g + 1;
             const gf128 right = reversed ? src[cnt - 1 - ri] : src[ri];
@@ -945,9 +933,8 @@ __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ K
             dst[g] = v;
         }
         __syncthreads();
-        gf128 *tmp = src;
+        if (half <= 1024) flip ^= 1;
         src = dst;
-        dst = tmp;
         reversed = false;
         cnt = half;
         level++;
