@@ -182,6 +182,24 @@ def dist_setup(n_gpus):
     return rank, local, world
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest of every rank's x (the slowest rank's time); x itself at
+    N=1.  `dist` is torch.distributed with an initialised process group."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(world: int, bytes_per_step_per_rank: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: the bytes all ranks processed / the max-over-ranks
+    time (weak scaling: every rank processes the same work)."""
+    return world * bytes_per_step_per_rank * steps / seconds / 1e9
+
+
 def run_reference(args):
     rank, local, world = dist_setup(args.gpus)
     if rank != 0:
@@ -294,12 +312,9 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = _native.gcm_profile_read(ctx.handle, reset=True)
     _native.gcm_profile_enable(ctx.handle, False)
-    if dist is not None:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     bytes_per_step = 2 * padded
-    value = world * bytes_per_step * args.steps / (ms * 1e-3) / 1e9
+    value = whole_job_gbs(world, bytes_per_step, args.steps, ms * 1e-3)
 
     # ---- per-direction device throughput (secondary) ----
     barrier()
@@ -370,14 +385,11 @@ def run_ours(args):
             host_step()
         barrier()
         dt = time.perf_counter() - t0
-        if dist is not None:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(dt, dist)
         if not torch.equal(h_back, h_pt):
             raise SystemExit("host round trip mismatch")
         e2e = {
-            "value": world * bytes_per_step * ksteps / dt / 1e9,
+            "value": whole_job_gbs(world, bytes_per_step, ksteps, dt),
             "unit": "GB/s",
             "h2d_bytes_per_step": (2880 + padded) + (2880 + padded + 16),
             "d2h_bytes_per_step": (padded + 16) + (padded + 4),

@@ -203,8 +203,10 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
             return -1;
         }
     } else {
+        // With a 96-bit IV the caller forms J0 on the host and the combine
+        // kernel derives E_K(J0), so nothing per message is needed here.
         err = cudaStreamWaitEvent(s, e.ready, 0);
-        if (err == cudaSuccess) err = launch_msg_only(ks, s);
+        if (err == cudaSuccess && ks.iv_len != 12) err = launch_msg_only(ks, s);
         if (err != cudaSuccess) return -1;
     }
     e.tick = ++ctx->key_cache_tick;
@@ -316,6 +318,14 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kf.mm = mm;
     kf.tabs = ctx->tabs;
     kf.partials = partials;
+    if (iv_len == 12) {
+        // J0 = IV || 0^31 || 1 (SP 800-38D Alg. 4 step 2), as memory words.
+        kf.j0_given = 1u;
+        for (int i = 0; i < 3; i++)
+            kf.j0[i] = (uint32_t)iv[4 * i] | ((uint32_t)iv[4 * i + 1] << 8) | ((uint32_t)iv[4 * i + 2] << 16) |
+                       ((uint32_t)iv[4 * i + 3] << 24);
+        kf.j0[3] = 0x01000000u;
+    }
     const int grid = (int)((K < (uint64_t)ctx->num_sms) ? K : (uint64_t)ctx->num_sms);
     const bool prof = ctx->profiling.load() != 0 && K > 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -350,6 +360,11 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kc.tag_expected = decrypt ? tag_dev : nullptr;
     kc.status = status_dev;
     kc.raw = (mode == 2) ? 1 : 0;
+    kc.tabs = ctx->tabs;
+    if (kf.j0_given) {
+        kc.ej0_from_j0 = 1u;
+        for (int i = 0; i < 4; i++) kc.j0[i] = kf.j0[i];
+    }
     e = launch_combine(kc, s);
     if (e != cudaSuccess) return cuda_fail(e, "combine kernel launch");
     ctx->launches += 1;

@@ -125,6 +125,26 @@ __host__ __device__ __forceinline__ void clmul64(uint64_t a, uint64_t b, uint64_
     hi = p2 ^ (p1 >> 32);
 }
 
+// Reduces the 255-bit carry-less product P3:P2:P1:P0 (64-bit words, bit i =
+// coefficient of x^i, P3 < 2^63) modulo x^128 + x^7 + x^2 + x + 1 and returns
+// it as poly words.  x^128 = x^7 + x^2 + x + 1: the high half Q = P3:P2 folds
+// back as Q * (1 + x + x^2 + x^7).  Its bits pushed above x^127 (the top 7
+// bits of Q shifted by 1, 2, 7) fold once more; adding them into the low bits
+// of Q first (T) makes one pass of shifts do both folds.
+__host__ __device__ __forceinline__ void gf_reduce256(uint64_t P0, uint64_t P1, uint64_t P2, uint64_t P3,
+                                                      uint32_t out[4])
+{
+    const uint64_t T0 = P2 ^ (P3 >> 63) ^ (P3 >> 62) ^ (P3 >> 57);
+    const uint64_t T1 = P3;
+    const uint64_t R0 = T0 ^ (T0 << 1) ^ (T0 << 2) ^ (T0 << 7);
+    const uint64_t R1 = T1 ^ ((T1 << 1) | (T0 >> 63)) ^ ((T1 << 2) | (T0 >> 62)) ^ ((T1 << 7) | (T0 >> 57));
+    const uint64_t Z0 = P0 ^ R0, Z1 = P1 ^ R1;
+    out[0] = brev32((uint32_t)Z0);
+    out[1] = brev32((uint32_t)(Z0 >> 32));
+    out[2] = brev32((uint32_t)Z1);
+    out[3] = brev32((uint32_t)(Z1 >> 32));
+}
+
 // Product of two field elements given as poly words (see the top of this
 // file): out = a * b mod x^128 + x^7 + x^2 + x + 1.
 __host__ __device__ __forceinline__ void gf_mul_words(const uint32_t a[4], const uint32_t b[4], uint32_t out[4])
@@ -141,27 +161,44 @@ __host__ __device__ __forceinline__ void gf_mul_words(const uint32_t a[4], const
     clmul64(A0 ^ A1, B0 ^ B1, l1, h1);
     l1 ^= l0 ^ l2;
     h1 ^= h0 ^ h2;
-    // 255-bit product P3:P2:P1:P0 (64-bit words, P3 < 2^63).
-    const uint64_t P0 = l0, P1 = h0 ^ l1, P2 = l2 ^ h1, P3 = h2;
-    // x^128 = x^7 + x^2 + x + 1: the high half Q = P3:P2 folds back as
-    // Q * (1 + x + x^2 + x^7).  Its bits pushed above x^127 (the top 7 bits
-    // of Q shifted by 1, 2, 7) fold once more; adding them into the low bits
-    // of Q first (T) makes one pass of shifts do both folds.
-    const uint64_t T0 = P2 ^ (P3 >> 63) ^ (P3 >> 62) ^ (P3 >> 57);
-    const uint64_t T1 = P3;
-    const uint64_t R0 = T0 ^ (T0 << 1) ^ (T0 << 2) ^ (T0 << 7);
-    const uint64_t R1 = T1 ^ ((T1 << 1) | (T0 >> 63)) ^ ((T1 << 2) | (T0 >> 62)) ^ ((T1 << 7) | (T0 >> 57));
-    const uint64_t Z0 = P0 ^ R0, Z1 = P1 ^ R1;
-    out[0] = brev32((uint32_t)Z0);
-    out[1] = brev32((uint32_t)(Z0 >> 32));
-    out[2] = brev32((uint32_t)Z1);
-    out[3] = brev32((uint32_t)(Z1 >> 32));
+    gf_reduce256(l0, h0 ^ l1, l2 ^ h1, h2, out);
 }
 
 __device__ __forceinline__ gf128 gf_mul(const gf128 &a, const gf128 &b)
 {
     gf128 r;
     gf_mul_words(a.w, b.w, r.w);
+    return r;
+}
+
+// The same product computed by a whole warp, for a multiply on a serial
+// path (the tree combine, the tag): every lane passes the same a and b and
+// receives a * b.  Lanes 0..15 each form one of the 16 schoolbook products
+// of 32-bit words, A_i * B_j at bit offset 32 (i + j); every lane then sums
+// them from `scratch` (16 x 8 bytes of shared memory owned by this warp) and
+// reduces the 255-bit product.  Several hundred cycles instead of the
+// several thousand of one thread doing all nine Karatsuba products.
+__device__ __forceinline__ gf128 gf_mul_warp(const gf128 &a, const gf128 &b, uint64_t *scratch)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane < 16) {
+        const int i = lane >> 2, j = lane & 3;
+        scratch[lane] = clmul32(brev32(a.w[i]), brev32(b.w[j]));
+    }
+    __syncwarp();
+    uint32_t p[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint64_t v = scratch[4 * i + j];
+            p[i + j] ^= (uint32_t)v;
+            p[i + j + 1] ^= (uint32_t)(v >> 32);
+        }
+    __syncwarp();  // scratch may be reused by the next call
+    gf128 r;
+    gf_reduce256((uint64_t)p[0] | ((uint64_t)p[1] << 32), (uint64_t)p[2] | ((uint64_t)p[3] << 32),
+                 (uint64_t)p[4] | ((uint64_t)p[5] << 32), (uint64_t)p[6] | ((uint64_t)p[7] << 32), r.w);
     return r;
 }
 

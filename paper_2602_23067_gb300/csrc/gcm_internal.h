@@ -29,7 +29,8 @@ constexpr uint32_t SM_T23 = 65536;     // rows v: [T2[v] x 32 lanes | T3[v] x 32
 constexpr uint32_t SM_GTAB = 131072;   // rows v: 16 positions x 16 bytes
 constexpr uint32_t SM_RED = 196608;    // cross-warp reduction slots (16 x 16 B)
 constexpr uint32_t SM_SEGF = SM_RED + 256;  // per-warp segment factors H^((15-w)S)
-constexpr uint32_t KF_SMEM_BYTES = SM_SEGF + KF_WARPS * 16;
+constexpr uint32_t SM_WSCR = SM_SEGF + KF_WARPS * 16;  // per-warp scratch of gf_mul_warp (16 x 128 B)
+constexpr uint32_t KF_SMEM_BYTES = SM_WSCR + KF_WARPS * 128;
 
 // Per-key material, built on the device by the key-setup kernel.
 struct KeyMat {
@@ -87,6 +88,8 @@ struct KfParams {
     const MsgMat *mm;
     const DevTables *tabs;
     gf128 *partials;        // K tile partials, poly words
+    uint32_t j0_given;      // 1: J0 is j0 below (96-bit IV, formed on the host), else mm->j0
+    uint32_t j0[4];         // memory words
 };
 
 // One message of a device-memory batch (gcm_batch with GCM_MEM_DEVICE).
@@ -139,6 +142,9 @@ struct KcParams {
     const uint8_t *tag_expected;  // 16 bytes (device) for decrypt, else null
     int32_t *status;        // device status word (decrypt), may be null
     int raw;                // 1: output GHASH_H(A, C) itself (no E_K(J0) mask)
+    uint32_t ej0_from_j0;   // 1: compute E_K(J0) here from j0 below, else read mm->ej0
+    uint32_t j0[4];         // memory words
+    const DevTables *tabs;  // round tables (for E_K(J0))
 };
 
 struct KzParams {

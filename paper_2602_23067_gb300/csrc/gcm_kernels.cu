@@ -40,16 +40,15 @@ __global__ void __launch_bounds__(256) build_tables_kernel(DevTables *tabs)
 
 // ---------------------------------------------------------------------
 // Single-block AES for the setup kernels (H = E_K(0^128) and E_K(J0)):
-// the context's round tables T0..T3 and S-box, read through the read-only
-// cache.  State: four memory words, word c = column c, byte r = row r;
+// round tables T0..T3 and S-box given by pointer (the context's tables in
+// global memory, or a copy in shared memory).  State: four memory words, word c = column c, byte r = row r;
 // column c of a round takes row r from column c + r (ShiftRows).
 // ---------------------------------------------------------------------
-__device__ void aes_block_tt(const uint32_t *rk, int nr, const DevTables *tabs, const uint32_t in[4],
-                             uint32_t out[4])
+__device__ void aes_block_tt(const uint32_t *rk, int nr, const uint32_t *T, const uint8_t *sbox,
+                             const uint32_t in[4], uint32_t out[4])
 {
-    const uint32_t *T = tabs->ttab;
     uint32_t s0 = in[0] ^ rk[0], s1 = in[1] ^ rk[1], s2 = in[2] ^ rk[2], s3 = in[3] ^ rk[3];
-#define TT(k, w, B) __ldg(&T[(k) * 256 + (((w) >> (8 * (B))) & 0xFFu)])
+#define TT(k, w, B) T[(k) * 256 + (((w) >> (8 * (B))) & 0xFFu)]
     for (int r = 1; r < nr; r++) {
         const uint32_t n0 = TT(0, s0, 0) ^ TT(1, s1, 1) ^ TT(2, s2, 2) ^ TT(3, s3, 3) ^ rk[4 * r];
         const uint32_t n1 = TT(0, s1, 0) ^ TT(1, s2, 1) ^ TT(2, s3, 2) ^ TT(3, s0, 3) ^ rk[4 * r + 1];
@@ -58,7 +57,7 @@ __device__ void aes_block_tt(const uint32_t *rk, int nr, const DevTables *tabs, 
         s0 = n0; s1 = n1; s2 = n2; s3 = n3;
     }
 #undef TT
-#define SB(w, B) ((uint32_t)__ldg(&tabs->sbox[((w) >> (8 * (B))) & 0xFFu]) << (8 * (B)))
+#define SB(w, B) ((uint32_t)sbox[((w) >> (8 * (B))) & 0xFFu] << (8 * (B)))
     out[0] = (SB(s0, 0) | SB(s1, 1) | SB(s2, 2) | SB(s3, 3)) ^ rk[4 * nr];
     out[1] = (SB(s1, 0) | SB(s2, 1) | SB(s3, 2) | SB(s0, 3)) ^ rk[4 * nr + 1];
     out[2] = (SB(s2, 0) | SB(s3, 1) | SB(s0, 2) | SB(s1, 3)) ^ rk[4 * nr + 2];
@@ -116,7 +115,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         int nr = key_expand_words(key, (int)key_len, sbox, rkw);
         s_nr = nr;
         uint32_t zero[4] = {0u, 0u, 0u, 0u}, h[4];
-        aes_block_tt(rkw, nr, tabs, zero, h);
+        aes_block_tt(rkw, nr, tabs->ttab, tabs->sbox, zero, h);
         sH = gf_from_mem(h[0], h[1], h[2], h[3]);
     }
     __syncthreads();
@@ -156,7 +155,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
             j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
         }
         uint32_t e[4];
-        aes_block_tt(rkw, nr, tabs, j0, e);
+        aes_block_tt(rkw, nr, tabs->ttab, tabs->sbox, j0, e);
         for (int i = 0; i < 4; i++) {
             mm->j0[i] = j0[i];
             mm->ej0[i] = e[i];
@@ -387,13 +386,14 @@ struct MsgConst {
 };
 
 __device__ __forceinline__ MsgConst make_msg_const(const uint8_t *t01, const uint8_t *t23, const LaneConst &L,
-                                                   const KeyMat *km, const MsgMat *mm)
+                                                   const KeyMat *km, uint32_t j0w0, uint32_t j0w1, uint32_t j0w2,
+                                                   uint32_t j0w3)
 {
     MsgConst c;
-    c.j0w0 = __ldg(&mm->j0[0]);
-    c.j0w1 = __ldg(&mm->j0[1]);
-    c.j0w2 = __ldg(&mm->j0[2]);
-    c.ctr0 = bswap32(__ldg(&mm->j0[3]));
+    c.j0w0 = j0w0;
+    c.j0w1 = j0w1;
+    c.j0w2 = j0w2;
+    c.ctr0 = bswap32(j0w3);
     const uint32_t x0 = c.j0w0 ^ __ldg(&km->rk[0]);
     const uint32_t x1 = c.j0w1 ^ __ldg(&km->rk[1]);
     const uint32_t x2 = c.j0w2 ^ __ldg(&km->rk[2]);
@@ -409,11 +409,15 @@ __device__ __forceinline__ MsgConst make_msg_const(const uint8_t *t01, const uin
 // Stages the replicated round tables into shared memory.
 __device__ __forceinline__ void stage_round_tables(uint8_t *smem, const DevTables *tabs)
 {
+    // Row v of a region holds T_even[v] for the 32 lanes, then T_odd[v]:
+    // 16 vectors of four equal words.
     const uint32_t *tt = tabs->ttab;
-    uint32_t *s32 = reinterpret_cast<uint32_t *>(smem);
-    for (int w = threadIdx.x; w < 32768; w += KF_THREADS) {
-        const int region = w >> 14, v = (w >> 6) & 255, odd = (w >> 5) & 1;
-        s32[w] = __ldg(&tt[(2 * region + odd) * 256 + v]);
+    uint4 *s128 = reinterpret_cast<uint4 *>(smem);
+#pragma unroll 4
+    for (int q = threadIdx.x; q < 8192; q += KF_THREADS) {
+        const int region = q >> 12, v = (q >> 4) & 255, odd = (q >> 3) & 1;
+        const uint32_t t = __ldg(&tt[(2 * region + odd) * 256 + v]);
+        s128[q] = make_uint4(t, t, t, t);
     }
 }
 
@@ -607,7 +611,11 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
         for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
-    if (lane == 0) red[warp] = (warp == KF_WARPS - 1) ? z : gf_mul(z, segf[warp]);
+    // Every lane holds the warp's sum z; the whole warp multiplies it by the
+    // segment factor (warp-uniform branch).
+    if (warp != KF_WARPS - 1)
+        z = gf_mul_warp(z, segf[warp], reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
+    if (lane == 0) red[warp] = z;
     __syncthreads();
     if (warp == 0) {
         z = (lane < KF_WARPS) ? red[lane] : gf_zero();
@@ -650,7 +658,9 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
     v.mm = p.mm;
     v.partials = p.partials;
     __syncthreads();
-    const MsgConst c = make_msg_const(t01, t23, L, p.km, p.mm);
+    const MsgConst c = p.j0_given ? make_msg_const(t01, t23, L, p.km, p.j0[0], p.j0[1], p.j0[2], p.j0[3])
+                                  : make_msg_const(t01, t23, L, p.km, __ldg(&p.mm->j0[0]), __ldg(&p.mm->j0[1]),
+                                                   __ldg(&p.mm->j0[2]), __ldg(&p.mm->j0[3]));
     GroupCache gc;
     gc.grp = 0xFFFFFFFFu;
     gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
@@ -670,7 +680,8 @@ __device__ __noinline__ void batch_tile(uint8_t *smem, const MsgView &v, const L
     uint32_t rk[4 * (NR + 1)];
 #pragma unroll
     for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&v.km->rk[i]);
-    const MsgConst c = make_msg_const(t01, t23, L, v.km, v.mm);
+    const MsgConst c = make_msg_const(t01, t23, L, v.km, __ldg(&v.mm->j0[0]), __ldg(&v.mm->j0[1]),
+                                      __ldg(&v.mm->j0[2]), __ldg(&v.mm->j0[3]));
     tile_body<NR>(smem, v, c, rk, L, tile, gc);
 }
 
@@ -857,7 +868,7 @@ __device__ void msg_material(const uint8_t *iv, uint32_t iv_len, const KeyMat *k
         j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
     }
     uint32_t e[4];
-    aes_block_tt(km->rk, (int)km->nr, tabs, j0, e);
+    aes_block_tt(km->rk, (int)km->nr, tabs->ttab, tabs->sbox, j0, e);
     for (int i = 0; i < 4; i++) {
         mm->j0[i] = j0[i];
         mm->ej0[i] = e[i];
@@ -903,13 +914,22 @@ __global__ void __launch_bounds__(256) batch_key_setup_kernel(const BatchMsg *ms
 // ---------------------------------------------------------------------
 // KC: log-depth combine + tag (one CTA)
 // ---------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ KcParams p)
+__global__ void __launch_bounds__(512) combine_kernel(const __grid_constant__ KcParams p)
 {
     // Levels whose output fits (at most 1024 entries) run in shared memory;
-    // larger ones go through the global scratch.
+    // larger ones go through the global scratch.  Levels with many products
+    // give one product to each thread; levels with few give each product to
+    // a whole warp (gf_mul_warp), which has a much shorter latency.
     __shared__ gf128 sbuf[2][1024];
-    const int t = threadIdx.x;
+    __shared__ uint64_t wscr[16][16];
+    __shared__ uint32_t stab[1024];
+    __shared__ uint8_t ssbox[256];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
     const KeyMat *km = p.km;
+    if (p.ej0_from_j0) {
+        for (int i = t; i < 1024; i += blockDim.x) stab[i] = __ldg(&p.tabs->ttab[i]);
+        for (int i = t; i < 256; i += blockDim.x) ssbox[i] = __ldg(&p.tabs->sbox[i]);
+    }
     uint64_t cnt = p.K;
     int level = 0;
     // Level 0 reads the partials right to left (index g counts tiles from
@@ -922,15 +942,20 @@ __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ K
         const uint64_t half = (cnt + 1) / 2;
         const gf128 mult = km->h2k[p.tile_log2 + level];
         gf128 *dst = (half <= 1024) ? sbuf[flip] : ((src == p.scratch) ? p.partials : p.scratch);
-        for (uint64_t g = t; g < half; g += blockDim.x) {
-            const uint64_t ri = 2 * g, li = 2 * g + 1;
-            const gf128 right = reversed ? src[cnt - 1 - ri] : src[ri];
-            gf128 v = right;
-            if (li < cnt) {
-                const gf128 left = reversed ? src[cnt - 1 - li] : src[li];
-                v = gf_xor(gf_mul(left, mult), right);
+        if (half > (uint64_t)nwarps * 4) {
+            for (uint64_t g = t; g < half; g += blockDim.x) {
+                const uint64_t ri = 2 * g, li = 2 * g + 1;
+                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
+                if (li < cnt) v = gf_xor(gf_mul(reversed ? src[cnt - 1 - li] : src[li], mult), v);
+                dst[g] = v;
             }
-            dst[g] = v;
+        } else {
+            for (uint64_t g = warp; g < half; g += nwarps) {
+                const uint64_t ri = 2 * g, li = 2 * g + 1;
+                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
+                if (li < cnt) v = gf_xor(gf_mul_warp(reversed ? src[cnt - 1 - li] : src[li], mult, wscr[warp]), v);
+                if (lane == 0) dst[g] = v;
+            }
         }
         __syncthreads();
         if (half <= 1024) flip ^= 1;
@@ -939,31 +964,35 @@ __global__ void __launch_bounds__(1024) combine_kernel(const __grid_constant__ K
         cnt = half;
         level++;
     }
-    if (t == 0) {
-        gf128 s = (cnt == 1) ? src[0] : gf_zero();
-        // Length block [len(A)]_64 || [len(C)]_64 in bits (SP 800-38D Alg. 4 step 5).
-        gf128 lb;
-        const uint64_t abits = p.aad_len * 8u, cbits = p.len * 8u;
-        lb.w[0] = (uint32_t)(abits >> 32);
-        lb.w[1] = (uint32_t)abits;
-        lb.w[2] = (uint32_t)(cbits >> 32);
-        lb.w[3] = (uint32_t)cbits;
-        const gf128 gh = gf_mul(gf_xor(s, lb), km->H);
-        const uint4 gm = gf_to_mem(gh);
-        const uint32_t mask[4] = {p.raw ? 0u : p.mm->ej0[0], p.raw ? 0u : p.mm->ej0[1], p.raw ? 0u : p.mm->ej0[2],
-                                  p.raw ? 0u : p.mm->ej0[3]};
-        const uint32_t tw[4] = {gm.x ^ mask[0], gm.y ^ mask[1], gm.z ^ mask[2], gm.w ^ mask[3]};
-        uint8_t tag[16];
-        for (int b = 0; b < 16; b++) tag[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
-        if (p.tag_out)
-            for (int b = 0; b < 16; b++) p.tag_out[b] = tag[b];
-        if (p.tag_expected) {
-            uint32_t diff = 0;
-            for (int b = 0; b < 16; b++) diff |= (uint32_t)(tag[b] ^ p.tag_expected[b]);
-            if (p.status) *p.status = diff ? -3 : 0;
-        } else if (p.status) {
-            *p.status = 0;
+    if (warp != 0) return;
+    gf128 s = (cnt == 1) ? src[0] : gf_zero();
+    // Length block [len(A)]_64 || [len(C)]_64 in bits (SP 800-38D Alg. 4 step 5).
+    gf128 lb;
+    const uint64_t abits = p.aad_len * 8u, cbits = p.len * 8u;
+    lb.w[0] = (uint32_t)(abits >> 32);
+    lb.w[1] = (uint32_t)abits;
+    lb.w[2] = (uint32_t)(cbits >> 32);
+    lb.w[3] = (uint32_t)cbits;
+    const gf128 gh = gf_mul_warp(gf_xor(s, lb), km->H, wscr[0]);
+    if (lane != 0) return;
+    const uint4 gm = gf_to_mem(gh);
+    uint32_t ej0[4] = {0u, 0u, 0u, 0u};
+    if (!p.raw) {
+        if (p.ej0_from_j0) {
+            aes_block_tt(km->rk, (int)km->nr, stab, ssbox, p.j0, ej0);
+        } else {
+            for (int i = 0; i < 4; i++) ej0[i] = p.mm->ej0[i];
         }
+    }
+    const uint32_t tw[4] = {gm.x ^ ej0[0], gm.y ^ ej0[1], gm.z ^ ej0[2], gm.w ^ ej0[3]};
+    if (p.tag_out)
+        for (int b = 0; b < 16; b++) p.tag_out[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
+    if (p.tag_expected) {
+        uint32_t diff = 0;
+        for (int b = 0; b < 16; b++) diff |= (uint32_t)((uint8_t)(tw[b >> 2] >> (8 * (b & 3))) ^ p.tag_expected[b]);
+        if (p.status) *p.status = diff ? -3 : 0;
+    } else if (p.status) {
+        *p.status = 0;
     }
 }
 
@@ -1079,7 +1108,7 @@ cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t strea
 
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream)
 {
-    combine_kernel<<<1, 1024, 0, stream>>>(p);
+    combine_kernel<<<1, 512, 0, stream>>>(p);
     return cudaGetLastError();
 }
 
