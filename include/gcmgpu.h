@@ -122,6 +122,32 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
  * counterpart in the paper, which sets up the key per call. */
 int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
 
+/* Tile size of the single-message calls.  The fused pass splits the GHASH
+ * input sequence A || C into tiles of 2^t 16-byte blocks (the paper's chunks,
+ * Sec. 5.2.3 map phase); any t gives the same ciphertext and tag.  By
+ * default t comes from the autotuned table below, else from a rule (t = 16,
+ * lowered down to 9 while there are fewer than 4 tiles per SM).
+ * gcm_ctx_set_tile_log2 forces t = tile_log2 (9..16) for every call; 0
+ * returns to the default. */
+int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2);
+
+/* Autotuner (the analogue of the paper's per-GPU (TS, R) search, Sec. 5.3,
+ * Table "Kernel-optimal parameters"): times a GCM encryption of
+ * 16 KiB, 64 KiB, 256 KiB, ... (x4) up to max_bytes (at most 1 GiB) of
+ * device-resident zeros with a key of key_len bytes for every tile size
+ * 2^9..2^16 blocks, and keeps the fastest per size class: table[c] is the
+ * chosen t for sequences of 2^c .. 2^(c+1)-1 blocks (0 = not tuned, the rule
+ * applies).  Classes between two measured sizes take the smaller size's
+ * choice; classes above the largest take the largest's.  Uses a private
+ * stream, about 2 x max_bytes of device scratch from the context's pool
+ * (subject to its budget) and synchronises.  table_out (64 bytes, may be
+ * NULL) receives the table.  No counterpart in the paper beyond its search. */
+int gcm_ctx_autotune(gcm_ctx *ctx, size_t key_len, size_t max_bytes, uint8_t *table_out);
+
+/* Installs a tuning table (64 entries, each 0 or 9..16), e.g. one saved
+ * from gcm_ctx_autotune on the same GPU model; NULL clears it. */
+int gcm_ctx_set_tuning(gcm_ctx *ctx, const uint8_t *table);
+
 /* Waits until everything enqueued on `stream` (a cudaStream_t; NULL is the
  * legacy default stream) has finished on the context's device, and reports
  * an asynchronous CUDA error from that work as GCM_ERR_CUDA.  The

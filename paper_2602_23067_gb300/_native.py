@@ -89,6 +89,9 @@ SIGNATURES = {
     "gcm_encrypt_noalloc": (ctypes.c_int, [_VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP]),
     "gcm_sync": (ctypes.c_int, [_VP, _VP]),
     "gcm_ctx_set_key_cache": (ctypes.c_int, [_VP, _SZ]),
+    "gcm_ctx_set_tile_log2": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "gcm_ctx_autotune": (ctypes.c_int, [_VP, _SZ, _SZ, _VP]),
+    "gcm_ctx_set_tuning": (ctypes.c_int, [_VP, _VP]),
     "gcm_ctr_xor": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP]),
     "gcm_ghash": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP]),
     "gfc_fits_layout": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(GfcLayout)]),

@@ -145,6 +145,24 @@ class Context:
         """gcm_ctx_set_key_cache: keys kept set up on the device (0 = off)."""
         check(lib.gcm_ctx_set_key_cache(self.handle, entries))
 
+    def set_tile_log2(self, tile_log2: int) -> None:
+        """gcm_ctx_set_tile_log2: force tiles of 2^tile_log2 blocks (0 = default)."""
+        check(lib.gcm_ctx_set_tile_log2(self.handle, tile_log2))
+
+    def autotune(self, key_len: int = 32, max_bytes: int = 256 << 20) -> bytes:
+        """gcm_ctx_autotune: returns the 64-entry table (tile log2 per size class)."""
+        buf = ctypes.create_string_buffer(64)
+        check(lib.gcm_ctx_autotune(self.handle, key_len, max_bytes, ctypes.addressof(buf)))
+        return buf.raw
+
+    def set_tuning(self, table: Optional[bytes]) -> None:
+        """gcm_ctx_set_tuning: install a saved table (None clears it)."""
+        if table is None:
+            check(lib.gcm_ctx_set_tuning(self.handle, None))
+            return
+        buf = ctypes.create_string_buffer(bytes(table), 64)
+        check(lib.gcm_ctx_set_tuning(self.handle, ctypes.addressof(buf)))
+
     def sync(self, stream=None) -> None:
         """gcm_sync: wait for the work enqueued on `stream` (default: torch's
         current stream) and raise GcmError on an asynchronous CUDA error."""

@@ -83,6 +83,20 @@ uint32_t tile_log2_for(uint64_t M, int num_sms)
     return lg;
 }
 
+int size_class(uint64_t M)
+{
+    int c = 0;
+    while (c < 63 && (M >> (c + 1)) != 0) c++;
+    return c;
+}
+
+uint32_t tile_log2_ctx(const gcm_ctx *ctx, uint64_t M)
+{
+    if (ctx->forced_tile_log2) return (uint32_t)ctx->forced_tile_log2;
+    const uint8_t t = ctx->tuned_lg[size_class(M)];
+    return t ? t : tile_log2_for(M, ctx->num_sms);
+}
+
 struct Scratch {
     void *base = nullptr;
     size_t bytes = 0;
@@ -239,7 +253,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     const uint64_t a_blocks = (aad_len + 15) / 16;
     const uint64_t n_blocks = (len + 15) / 16;
     const uint64_t M = a_blocks + n_blocks;
-    const uint32_t lg = tile_log2_for(M, ctx->num_sms);
+    const uint32_t lg = tile_log2_ctx(ctx, M);
     const uint64_t K = (M + (1ull << lg) - 1) >> lg;
     uint32_t levels = 0;
     while ((1ull << levels) < K) levels++;
@@ -727,6 +741,110 @@ int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries)
         ctx->key_cache.clear();
     }
     ctx->key_cache_cap = entries;
+    return GCM_OK;
+}
+
+int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (tile_log2 != 0 && (tile_log2 < SEGF_MIN_LOG2 || tile_log2 > 16))
+        return fail(GCM_ERR_INVALID_ARG, "tile_log2 must be 0 (automatic) or 9..16");
+    ctx->forced_tile_log2 = tile_log2;
+    return GCM_OK;
+}
+
+int gcm_ctx_autotune(gcm_ctx *ctx, size_t key_len, size_t max_bytes, uint8_t *table_out)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (key_len != 16 && key_len != 24 && key_len != 32) return fail(GCM_ERR_INVALID_ARG, "key must be 16, 24 or 32 bytes");
+    if (max_bytes < ((size_t)16 << 10)) return fail(GCM_ERR_INVALID_ARG, "max_bytes must be at least 16 KiB");
+    if (max_bytes > ((size_t)1 << 30)) max_bytes = (size_t)1 << 30;
+    DeviceGuard guard(ctx->device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the context's device");
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "creating the tuning stream");
+    Scratch buf;
+    int rc = scratch_alloc(ctx, 2 * max_bytes + 256, s, buf);
+    if (rc) {
+        cudaStreamDestroy(s);
+        return rc;
+    }
+    uint8_t *in = static_cast<uint8_t *>(buf.base), *out = in + max_bytes, *tag = out + max_bytes;
+    e = cudaMemsetAsync(in, 0, max_bytes, s);
+    uint8_t key[32], iv[12];
+    for (int i = 0; i < 32; i++) key[i] = (uint8_t)(0x5A ^ (17 * i));
+    for (int i = 0; i < 12; i++) iv[i] = (uint8_t)(0xC3 ^ (29 * i));
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+    const int saved_forced = ctx->forced_tile_log2;
+    uint8_t found[64] = {};
+    int prev_class = -1;
+    uint8_t prev_lg = 0;
+    // Sizes 16 KiB, 64 KiB, ... (x4) up to max_bytes; each measured size
+    // decides the classes from its own up to the next measured size.
+    for (size_t S = (size_t)16 << 10; e == cudaSuccess && rc == GCM_OK && S <= max_bytes; S *= 4) {
+        const uint64_t M = S / 16;
+        float best = 1e30f;
+        uint8_t best_lg = 0;
+        for (int lg = SEGF_MIN_LOG2; lg <= 16 && rc == GCM_OK && e == cudaSuccess; lg++) {
+            if ((M >> lg) == 0 && lg > SEGF_MIN_LOG2) break;  // one tile already
+            ctx->forced_tile_log2 = lg;
+            float t_best = 1e30f;
+            for (int rep = 0; rep < 4 && rc == GCM_OK && e == cudaSuccess; rep++) {
+                Scratch sc;
+                e = cudaEventRecord(ev0, s);
+                if (e != cudaSuccess) break;
+                rc = enqueue_device(ctx, key, key_len, iv, sizeof(iv), nullptr, 0, in, S, out, tag, false, nullptr,
+                                    sc, s);
+                if (sc.base) scratch_free(ctx, sc, s);
+                if (rc) break;
+                e = cudaEventRecord(ev1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+                if (rep > 0 && ms < t_best) t_best = ms;  // rep 0 warms up
+            }
+            if (t_best < best) {
+                best = t_best;
+                best_lg = (uint8_t)lg;
+            }
+        }
+        const int c = size_class(M);
+        if (best_lg) {
+            for (int k = prev_class + 1; k <= c && prev_class >= 0; k++) found[k] = prev_lg;
+            found[c] = best_lg;
+            prev_class = c;
+            prev_lg = best_lg;
+        }
+    }
+    for (int k = prev_class + 1; k < 64 && prev_class >= 0; k++) found[k] = prev_lg;
+    ctx->forced_tile_log2 = saved_forced;
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    scratch_free(ctx, buf, s);
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "autotuning");
+    memcpy(ctx->tuned_lg, found, sizeof(found));
+    if (table_out) memcpy(table_out, found, sizeof(found));
+    return GCM_OK;
+}
+
+int gcm_ctx_set_tuning(gcm_ctx *ctx, const uint8_t *table)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    uint8_t t[64] = {};
+    if (table) {
+        for (int i = 0; i < 64; i++) {
+            if (table[i] != 0 && (table[i] < SEGF_MIN_LOG2 || table[i] > 16))
+                return fail(GCM_ERR_INVALID_ARG, "tuning entries must be 0 or 9..16");
+            t[i] = table[i];
+        }
+    }
+    memcpy(ctx->tuned_lg, t, sizeof(t));
     return GCM_OK;
 }
 

@@ -64,6 +64,11 @@ struct gcm_ctx {
     std::vector<KeyCacheEntry> key_cache;
     size_t key_cache_cap = 64;
     uint64_t key_cache_tick = 0;
+    // Tile size of the single-message path: forced (gcm_ctx_set_tile_log2),
+    // else the autotuned choice for the sequence's size class
+    // (tuned_lg[floor(log2(blocks))], 0 = not tuned), else the built-in rule.
+    int forced_tile_log2 = 0;
+    uint8_t tuned_lg[64] = {};
 };
 
 namespace gcmgpu {
