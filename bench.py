@@ -390,12 +390,21 @@ def run_ours(args):
     e1.record(stream)
     barrier()
     ghash_ms = e0.elapsed_time(e1) / args.steps
+    tag_buf = torch.empty(16, dtype=torch.uint8, device="cuda")
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.encrypt_device(key, iv, d_aad, pt, ct=ctr_out, tag=tag_buf, stream=stream)
+    e1.record(stream)
+    barrier()
+    plain_ms = e0.elapsed_time(e1) / args.steps
     del ctr_out
     modes = {
         "ctr_only_gbs": padded / (ctr_ms * 1e-3) / 1e9,
         "ghash_only_gbs": (hl + padded) / (ghash_ms * 1e-3) / 1e9,
-        "gcm_encrypt_over_ctr_time": (padded / enc_gbs / 1e9) / (ctr_ms * 1e-3),
-        "api": "gcm_ctr_xor and gcm_ghash over the same data unit (device memory)",
+        "gcm_encrypt_over_ctr_time": (plain_ms * 1e-3) / (ctr_ms * 1e-3),
+        "gcm_encrypt_without_datasum_gbs": padded / (plain_ms * 1e-3) / 1e9,
+        "api": "gcm_ctr_xor, gcm_ghash and gcm_encrypt over the same data unit (device memory); the FITS calls of "
+               "the step also compute the DATASUM of the encrypted data unit in the same pass",
     }
 
     # ---- end to end through the C ABI with pinned host buffers ----

@@ -125,8 +125,10 @@ int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
 /* Tile size of the single-message calls.  The fused pass splits the GHASH
  * input sequence A || C into tiles of 2^t 16-byte blocks (the paper's chunks,
  * Sec. 5.2.3 map phase); any t gives the same ciphertext and tag.  By
- * default t comes from the autotuned table below, else from a rule (t = 16,
- * lowered down to 9 while there are fewer than 4 tiles per SM).
+ * default t comes from the context's tuning table (on a GB300 with 152 SMs a
+ * table measured there with gcm_ctx_autotune is installed at creation),
+ * else from a rule (t = 16, lowered down to 9 while there are fewer than 4
+ * tiles per SM).
  * gcm_ctx_set_tile_log2 forces t = tile_log2 (9..16) for every call; 0
  * returns to the default. */
 int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2);
@@ -385,7 +387,15 @@ int gfc_fits_layout(const uint8_t *fits, size_t len, gfc_layout *out);
  * error_code: 0, or the negative gcm_status of the call.
  * warning_code: 0 full access; 2 payload suppressed (tag mismatch: the data
  *   unit in data_buffer is zero-filled and the header is returned as is).
- * error_message: text of the failure ("" on success). */
+ * error_message: text of the failure ("" on success).
+ * datasum / datasum_valid: the FITS DATASUM (32-bit ones' complement sum of
+ *   the big-endian 32-bit words; the keyword the paper's container writes,
+ *   Sec. 3.2.2) of the ENCRYPTED data unit -- the one written by
+ *   gfc_fits_encrypt, or the one read by gfc_fits_decrypt_verify, so that a
+ *   container's stored DATASUM can be checked -- computed in the same pass as
+ *   the cipher (no extra read of the data).  datasum_valid is 1 when it was
+ *   computed (device memory, or host memory the GPU reads directly), 0 on the
+ *   staged host path. */
 typedef struct {
     uint8_t *data_buffer;
     size_t buffer_size;
@@ -394,6 +404,8 @@ typedef struct {
     char error_message[200];
     int mem;
     void *stream;
+    uint32_t datasum;
+    int datasum_valid;
 } gfc_result;
 
 /* Encrypts the data unit of a single-HDU FITS file and authenticates it

@@ -69,6 +69,8 @@ def lib():
         L.oracle_sbox.argtypes = [u8p, u8p]
         L.oracle_gf8_mul.argtypes = [ctypes.c_uint8, ctypes.c_uint8]
         L.oracle_gf8_mul.restype = ctypes.c_uint8
+        L.oracle_datasum.argtypes = [u8p, ctypes.c_size_t]
+        L.oracle_datasum.restype = ctypes.c_uint32
         _lib = L
     return _lib
 
@@ -300,6 +302,13 @@ def _card_value(card: bytes) -> Optional[str]:
     if "/" in v:
         v = v.split("/", 1)[0]
     return v.strip()
+
+
+def datasum(data: bytes) -> int:
+    """FITS DATASUM: 32-bit ones' complement sum of big-endian words with
+    end-around carry (C oracle, word by word)."""
+    b = _buf(bytes(data))
+    return int(lib().oracle_datasum(_ptr(b), len(data)))
 
 
 def fits_split(fits: bytes) -> Tuple[bytes, bytes, int]:

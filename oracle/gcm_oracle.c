@@ -444,3 +444,22 @@ int oracle_gcm_h_j0(const uint8_t *key, size_t key_len, const uint8_t *iv,
     if (EJ0) oracle_aes_encrypt_block(w, Nr, J0, EJ0);
     return 0;
 }
+
+/* FITS DATASUM (the FITS checksum convention of Seaman, Pence and Rots,
+ * which the paper's container writes through cfitsio, Sec. 3.2.2): the
+ * 32-bit ones' complement sum of the data read as big-endian 32-bit words,
+ * accumulated one word at a time with end-around carry.  A trailing partial
+ * word is padded with zero bytes. */
+uint32_t oracle_datasum(const uint8_t *data, size_t len)
+{
+    uint32_t sum = 0;
+    for (size_t i = 0; i < len; i += 4) {
+        uint32_t w = 0;
+        for (size_t b = 0; b < 4; b++)
+            w = (w << 8) | (i + b < len ? data[i + b] : 0u);
+        uint32_t t = sum + w;
+        if (t < w) t += 1; /* carry out of bit 31 wraps around to bit 0 */
+        sum = t;
+    }
+    return sum;
+}

@@ -51,7 +51,7 @@ class GfcLayout(ctypes.Structure):
 class GfcResult(ctypes.Structure):
     _fields_ = [("data_buffer", ctypes.c_void_p), ("buffer_size", ctypes.c_size_t), ("error_code", ctypes.c_int),
                 ("warning_code", ctypes.c_int), ("error_message", ctypes.c_char * 200), ("mem", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("datasum", ctypes.c_uint32), ("datasum_valid", ctypes.c_int)]
 
 
 class GcmMsg(ctypes.Structure):

@@ -27,13 +27,16 @@ class FitsResult:
     header in clear and the processed data unit; ``warning_code`` is 2 when
     the payload was suppressed after a tag mismatch."""
 
-    def __init__(self, data, error_code: int, warning_code: int, message: str, iv: bytes = b"", tag: bytes = b""):
+    def __init__(self, data, error_code: int, warning_code: int, message: str, iv: bytes = b"", tag: bytes = b"",
+                 datasum: Optional[int] = None):
         self.data = data
         self.error_code = error_code
         self.warning_code = warning_code
         self.message = message
         self.iv = iv
         self.tag = tag
+        # FITS DATASUM of the encrypted data unit (None when not computed)
+        self.datasum = datasum
 
 
 def _host_buf(data) -> Tuple[int, int, object]:
@@ -325,11 +328,14 @@ class Context:
                 data = _dev_tensor_copy(res.data_buffer, n, fits.device)
             else:
                 data = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(res.data_buffer)).copy()
+        datasum = int(res.datasum) if res.datasum_valid else None
+        warning = res.warning_code
+        if res.data_buffer:
             lib.gfc_result_free(self.handle, ctypes.byref(res))
         if rc not in (GCM_OK, GCM_ERR_AUTH):
             raise GcmError(rc, msg)
-        return FitsResult(data, rc, res.warning_code, msg, iv_out.raw if not decrypt else bytes(iv),
-                          tag_out.raw if not decrypt else bytes(tag))
+        return FitsResult(data, rc, warning, msg, iv_out.raw if not decrypt else bytes(iv),
+                          tag_out.raw if not decrypt else bytes(tag), datasum)
 
     def fits_encrypt_raw(self, key: bytes, fits, iv: bytes, aad_mode: int = GFC_AAD_HEADER, stream=None):
         """gfc_fits_encrypt on a CUDA tensor without copying the result: returns

@@ -90,6 +90,15 @@ int size_class(uint64_t M)
     return c;
 }
 
+// Tile sizes found by gcm_ctx_autotune on a GB300 (152 SMs, compute
+// capability 10.3) for AES-256-GCM, 16 KiB .. 1 GiB, indexed by
+// floor(log2(blocks)); installed by default on that device.  Medium messages
+// prefer about one tile per SM over the rule's four.
+const uint8_t kTunedGB300[64] = {
+    0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  9,  9,  9,  9,  9,  9,  10, 10, 11, 11, 13, 13,
+    15, 15, 14, 14, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16,
+    16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
+
 uint32_t tile_log2_ctx(const gcm_ctx *ctx, uint64_t M)
 {
     if (ctx->forced_tile_log2) return (uint32_t)ctx->forced_tile_log2;
@@ -248,8 +257,9 @@ void key_cache_release(gcm_ctx *ctx, int slot, cudaStream_t s)
 int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
                    const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out,
                    uint8_t *tag_dev, bool decrypt, int32_t *status_dev, Scratch &sc, cudaStream_t s,
-                   int mode = 0)
+                   int mode = 0, uint32_t *datasum_dev = nullptr)
 {
+    if (datasum_dev && mode == 0) mode = 3;  // GCM plus the DATASUM of the ciphertext side
     const uint64_t a_blocks = (aad_len + 15) / 16;
     const uint64_t n_blocks = (len + 15) / 16;
     const uint64_t M = a_blocks + n_blocks;
@@ -265,7 +275,8 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     const size_t off_part = align_up(off_mm + sizeof(MsgMat), 256);
     const size_t off_tree = align_up(off_part + (size_t)K * sizeof(gf128), 256);
     const size_t off_iv = align_up(off_tree + (size_t)(K / 2 + 1) * sizeof(gf128), 256);
-    const size_t total = align_up(off_iv + (iv_len > IV_INLINE_MAX ? iv_len : 0), 256);
+    const size_t off_ds = align_up(off_iv + (iv_len > IV_INLINE_MAX ? iv_len : 0), 256);
+    const size_t total = align_up(off_ds + (mode == 3 ? (size_t)K * sizeof(uint32_t) : 0), 256);
     int rc = scratch_alloc(ctx, total, s, sc);
     if (rc) return rc;
     uint8_t *base = static_cast<uint8_t *>(sc.base);
@@ -332,6 +343,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kf.mm = mm;
     kf.tabs = ctx->tabs;
     kf.partials = partials;
+    if (mode == 3) kf.dsums = reinterpret_cast<uint32_t *>(base + off_ds);
     if (iv_len == 12) {
         // J0 = IV || 0^31 || 1 (SP 800-38D Alg. 4 step 2), as memory words.
         kf.j0_given = 1u;
@@ -375,6 +387,10 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     kc.status = status_dev;
     kc.raw = (mode == 2) ? 1 : 0;
     kc.tabs = ctx->tabs;
+    if (mode == 3 && K > 0) {
+        kc.dsums = kf.dsums;
+        kc.datasum_out = datasum_dev;
+    }
     if (kf.j0_given) {
         kc.ej0_from_j0 = 1u;
         for (int i = 0; i < 4; i++) kc.j0[i] = kf.j0[i];
@@ -398,10 +414,14 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     return GCM_OK;
 }
 
+// datasum (optional, host): receives the FITS DATASUM of the ciphertext side
+// computed in the same pass, and the call then waits for its stream; it is
+// left untouched (and *datasum_done false) on the staged host path.
 int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
              const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out, uint8_t *tag,
-             bool decrypt, int mem, void *stream)
+             bool decrypt, int mem, void *stream, uint32_t *datasum = nullptr, bool *datasum_done = nullptr)
 {
+    if (datasum_done) *datasum_done = false;
     int rc = check_common(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, tag, mem);
     if (rc) return rc;
     const bool aligned = ((((uintptr_t)in) | ((uintptr_t)out)) & 15u) == 0;
@@ -418,14 +438,17 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
         uint8_t *iob = static_cast<uint8_t *>(io.base);
         int32_t *d_status = reinterpret_cast<int32_t *>(iob);
         uint8_t *d_tag = iob + 64;
+        uint32_t *d_sum = datasum ? reinterpret_cast<uint32_t *>(iob + 128) : nullptr;
         cudaError_t e = cudaSuccess;
         if (decrypt) e = cudaMemcpyAsync(d_tag, tag, 16, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && d_sum) e = cudaMemsetAsync(d_sum, 0, 4, s);
         if (e != cudaSuccess) {
             scratch_free(ctx, io, s);
             return cuda_fail(e, "tag copy");
         }
         Scratch sc;
-        rc = enqueue_device(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, d_tag, decrypt, d_status, sc, s);
+        rc = enqueue_device(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, d_tag, decrypt, d_status, sc, s,
+                            0, d_sum);
         if (rc) {
             if (sc.base) scratch_free(ctx, sc, s);
             scratch_free(ctx, io, s);
@@ -436,10 +459,16 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
         uint8_t htag[16];
         e = cudaMemcpyAsync(decrypt ? (void *)&status : (void *)htag, decrypt ? (void *)d_status : (void *)d_tag,
                             decrypt ? sizeof(int32_t) : 16, cudaMemcpyDeviceToHost, s);
+        uint32_t hsum = 0;
+        if (e == cudaSuccess && d_sum) e = cudaMemcpyAsync(&hsum, d_sum, 4, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         scratch_free(ctx, io, s);
         if (e != cudaSuccess) return cuda_fail(e, "host-direct call");
         if (!decrypt) memcpy(tag, htag, 16);
+        if (d_sum) {
+            *datasum = hsum;
+            if (datasum_done) *datasum_done = true;
+        }
         if (decrypt && status != 0) return fail(GCM_ERR_AUTH, "authentication tag mismatch: output zero-filled");
         return GCM_OK;
     }
@@ -478,6 +507,7 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
     if (rc) return rc;
     uint8_t *iob = static_cast<uint8_t *>(io.base);
     int32_t *d_status = reinterpret_cast<int32_t *>(iob + off_status);
+    uint32_t *d_sum = datasum ? reinterpret_cast<uint32_t *>(iob + off_status + 128) : nullptr;
     uint8_t *d_tag = host ? iob + off_tag : tag;
     const uint8_t *d_aad = host ? iob + off_aad : aad;
     uint8_t *d_data = host ? iob + off_data : nullptr;
@@ -495,9 +525,16 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
         }
     }
 
+    if (d_sum) {
+        e = cudaMemsetAsync(d_sum, 0, 4, s);
+        if (e != cudaSuccess) {
+            scratch_free(ctx, io, s);
+            return cuda_fail(e, "memset");
+        }
+    }
     Scratch sc;
     rc = enqueue_device(ctx, key, key_len, iv, iv_len, d_aad, aad_len, d_in, len, d_out, d_tag, decrypt,
-                        d_status, sc, s);
+                        d_status, sc, s, 0, d_sum);
     if (rc) {
         if (sc.base) scratch_free(ctx, sc, s);
         scratch_free(ctx, io, s);
@@ -514,14 +551,20 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
         }
     }
     int32_t status = 0;
-    if (decrypt) {
+    uint32_t hsum = 0;
+    if (d_sum) e = cudaMemcpyAsync(&hsum, d_sum, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && decrypt) {
         e = cudaMemcpyAsync(&status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    } else if (host) {
+    } else if (e == cudaSuccess && (host || d_sum)) {
         e = cudaStreamSynchronize(s);
     }
     scratch_free(ctx, io, s);
     if (e != cudaSuccess) return cuda_fail(e, "synchronisation");
+    if (d_sum) {
+        *datasum = hsum;
+        if (datasum_done) *datasum_done = true;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "asynchronous kernel error");
     if (decrypt && status != 0) return fail(GCM_ERR_AUTH, "authentication tag mismatch: output zero-filled");
@@ -532,6 +575,13 @@ int run_call(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv
 
 namespace gcmgpu {
 int ctx_fail(int code, const char *msg) { return fail(code, "%s", msg); }
+int ctx_run_with_datasum(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                         const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out,
+                         uint8_t *tag, bool decrypt, int mem, void *stream, uint32_t *datasum, bool *datasum_done)
+{
+    return run_call(ctx, key, key_len, iv, iv_len, aad, aad_len, in, len, out, tag, decrypt, mem, stream, datasum,
+                    datasum_done);
+}
 int ctx_cuda_fail(cudaError_t e, const char *where) { return cuda_fail(e, where); }
 uint32_t choose_tile_log2(uint64_t M, int num_sms) { return tile_log2_for(M, num_sms); }
 cudaEvent_t ctx_take_event(gcm_ctx *ctx)
@@ -582,6 +632,12 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     if (e == cudaSuccess) {
         uint64_t keep = UINT64_MAX;  // keep freed scratch cached for later calls
         e = cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    if (e == cudaSuccess) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+        if (major == 10 && minor == 3 && ctx->num_sms == 152) memcpy(ctx->tuned_lg, kTunedGB300, sizeof(kTunedGB300));
     }
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tabs, sizeof(DevTables));
     if (e == cudaSuccess) e = launch_build_tables(ctx->tabs, nullptr);

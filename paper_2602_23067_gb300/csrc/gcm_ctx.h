@@ -74,6 +74,12 @@ struct gcm_ctx {
 namespace gcmgpu {
 // Shared between the C-ABI implementation files.
 int ctx_fail(int code, const char *msg);
+// gcm_encrypt / gcm_decrypt_verify that also return the FITS DATASUM of the
+// ciphertext side (when the data goes through the device pass; *datasum_done
+// tells).  Waits for the stream.
+int ctx_run_with_datasum(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
+                         const uint8_t *aad, size_t aad_len, const uint8_t *in, size_t len, uint8_t *out,
+                         uint8_t *tag, bool decrypt, int mem, void *stream, uint32_t *datasum, bool *datasum_done);
 int ctx_cuda_fail(cudaError_t e, const char *where);
 uint32_t choose_tile_log2(uint64_t M, int num_sms);
 void ctx_record_fused(gcm_ctx *ctx, cudaEvent_t start, cudaEvent_t stop, uint64_t bytes);

@@ -30,7 +30,8 @@ constexpr uint32_t SM_GTAB = 131072;   // rows v: 16 positions x 16 bytes
 constexpr uint32_t SM_RED = 196608;    // cross-warp reduction slots (16 x 16 B)
 constexpr uint32_t SM_SEGF = SM_RED + 256;  // per-warp segment factors H^((15-w)S)
 constexpr uint32_t SM_WSCR = SM_SEGF + KF_WARPS * 16;  // per-warp scratch of gf_mul_warp (16 x 128 B)
-constexpr uint32_t KF_SMEM_BYTES = SM_WSCR + KF_WARPS * 128;
+constexpr uint32_t SM_DSUM = SM_WSCR + KF_WARPS * 128;  // per-warp DATASUM partials (16 x 8 B)
+constexpr uint32_t KF_SMEM_BYTES = SM_DSUM + KF_WARPS * 8;
 
 // Per-key material, built on the device by the key-setup kernel.
 struct KeyMat {
@@ -90,6 +91,7 @@ struct KfParams {
     gf128 *partials;        // K tile partials, poly words
     uint32_t j0_given;      // 1: J0 is j0 below (96-bit IV, formed on the host), else mm->j0
     uint32_t j0[4];         // memory words
+    uint32_t *dsums;        // K per-tile DATASUM partials (mode 3 only)
 };
 
 // One message of a device-memory batch (gcm_batch with GCM_MEM_DEVICE).
@@ -145,6 +147,8 @@ struct KcParams {
     uint32_t ej0_from_j0;   // 1: compute E_K(J0) here from j0 below, else read mm->ej0
     uint32_t j0[4];         // memory words
     const DevTables *tabs;  // round tables (for E_K(J0))
+    const uint32_t *dsums;  // K per-tile DATASUM partials, or null
+    uint32_t *datasum_out;  // device: the message's DATASUM (when dsums is set)
 };
 
 struct KzParams {
@@ -158,7 +162,8 @@ cudaError_t launch_build_tables(DevTables *tabs, cudaStream_t stream);
 cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
 // J0 and E_K(J0) only, into p.mm, for key material p.km set up earlier.
 cudaError_t launch_msg_only(const KsParams &p, cudaStream_t stream);
-// mode: 0 full GCM, 1 CTR keystream only, 2 GHASH only (no AES, no output)
+// mode: 0 full GCM, 1 CTR keystream only, 2 GHASH only (no AES, no output),
+// 3 full GCM plus the per-tile DATASUM partials of the ciphertext side
 cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode = 0);
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
 cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);

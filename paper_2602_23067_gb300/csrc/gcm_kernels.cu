@@ -365,6 +365,25 @@ __device__ __forceinline__ uint4 keep_bytes(const uint4 &v, uint32_t nbytes)
 constexpr int MODE_GCM = 0;
 constexpr int MODE_CTR = 1;
 constexpr int MODE_GHASH = 2;
+// Full GCM plus the FITS DATASUM of the ciphertext side: the 32-bit ones'
+// complement sum of the payload as big-endian words (zero-padded to a word),
+// taken over the same blocks GHASH hashes, so it costs no extra load.
+constexpr int MODE_GCM_SUM = 3;
+
+// Sum of the four big-endian 32-bit words of a 16-byte block.
+__device__ __forceinline__ uint64_t word_sum_be(const uint4 &x)
+{
+    return (uint64_t)bswap32(x.x) + bswap32(x.y) + (uint64_t)bswap32(x.z) + bswap32(x.w);
+}
+
+// Folds a 64-bit sum of 32-bit words into their 32-bit ones' complement sum
+// (end-around carry): the result is 0 only for a zero sum, else the sum
+// mod 2^32 - 1 with 0xFFFFFFFF standing for a nonzero multiple.
+__device__ __forceinline__ uint32_t ones_fold(uint64_t s)
+{
+    while (s >> 32) s = (s & 0xFFFFFFFFull) + (s >> 32);
+    return (uint32_t)s;
+}
 
 // Everything a tile needs to know about its message.
 struct MsgView {
@@ -377,6 +396,7 @@ struct MsgView {
     const KeyMat *km;
     const MsgMat *mm;
     gf128 *partials;
+    uint32_t *dsums;  // per-tile DATASUM partials (MODE_GCM_SUM)
 };
 
 // Per-message constants of AES round 1: everything except the lookups of
@@ -479,6 +499,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     uint32_t dlast = 0;
     bool have = false;
     uint32_t seg_len = 0;
+    uint64_t dsum = 0;  // MODE_GCM_SUM: this lane's word sum (< 2^45 per tile)
 
     if (seg_hi > seg_lo) {
         seg_len = (uint32_t)(seg_hi - seg_lo);
@@ -539,12 +560,14 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 if (active) {
                     ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
                     __stcs(out + d, ks);
-                    if (MODE == MODE_GCM) {
+                    if (MODE == MODE_GCM || MODE == MODE_GCM_SUM) {
+                        const uint4 x = v.dec ? din : ks;
                         uint4 m = ghash_mul_table(smem, acc, L);
-                        xor4(m, v.dec ? din : ks);
+                        xor4(m, x);
                         acc = m;
                         dlast = d;
                         have = true;
+                        if (MODE == MODE_GCM_SUM) dsum += word_sum_be(x);
                     }
                 }
             }
@@ -596,6 +619,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                     acc = m;
                     dlast = q;
                     have = true;
+                    if (MODE == MODE_GCM_SUM && s >= v.a_blocks) dsum += word_sum_be(x);
                 }
             }
         }
@@ -616,6 +640,12 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     if (warp != KF_WARPS - 1)
         z = gf_mul_warp(z, segf[warp], reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
     if (lane == 0) red[warp] = z;
+    uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
+    if (MODE == MODE_GCM_SUM) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, off);
+        if (lane == 0) dred[warp] = dsum;
+    }
     __syncthreads();
     if (warp == 0) {
         z = (lane < KF_WARPS) ? red[lane] : gf_zero();
@@ -624,6 +654,12 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
 #pragma unroll
             for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
         if (lane == 0) v.partials[tile] = z;
+        if (MODE == MODE_GCM_SUM) {
+            dsum = (lane < KF_WARPS) ? dred[lane] : 0ull;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, off);
+            if (lane == 0) v.dsums[tile] = ones_fold(dsum);
+        }
     }
     __syncthreads();
 }
@@ -657,6 +693,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
     v.km = p.km;
     v.mm = p.mm;
     v.partials = p.partials;
+    v.dsums = p.dsums;
     __syncthreads();
     const MsgConst c = p.j0_given ? make_msg_const(t01, t23, L, p.km, p.j0[0], p.j0[1], p.j0[2], p.j0[3])
                                   : make_msg_const(t01, t23, L, p.km, __ldg(&p.mm->j0[0]), __ldg(&p.mm->j0[1]),
@@ -783,6 +820,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         const uint32_t mi = s_msg;
         const BatchMsg &bm = p.msgs[mi];
         MsgView v;
+        v.dsums = nullptr;
         v.in = bm.in;
         v.out = bm.out;
         v.aad = bm.aad;
@@ -964,6 +1002,22 @@ __global__ void __launch_bounds__(512) combine_kernel(const __grid_constant__ Kc
         cnt = half;
         level++;
     }
+    if (p.dsums) {
+        // DATASUM: ones' complement total of the tile partials (each < 2^32,
+        // so a 64-bit sum cannot overflow for any supported length).
+        __shared__ uint64_t dpart[16];
+        uint64_t acc = 0;
+        for (uint64_t i = t; i < p.K; i += blockDim.x) acc += p.dsums[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+        if (lane == 0) dpart[warp] = acc;
+        __syncthreads();
+        if (t == 0) {
+            uint64_t tot = 0;
+            for (int w = 0; w < nwarps; w++) tot += dpart[w];
+            *p.datasum_out = ones_fold(tot);
+        }
+    }
     if (warp != 0) return;
     gf128 s = (cnt == 1) ? src[0] : gf_zero();
     // Length block [len(A)]_64 || [len(C)]_64 in bits (SP 800-38D Alg. 4 step 5).
@@ -1058,6 +1112,9 @@ cudaError_t configure_kernels()
     SET_SMEM((fused_kernel<12, MODE_CTR>));
     SET_SMEM((fused_kernel<14, MODE_CTR>));
     SET_SMEM((fused_kernel<14, MODE_GHASH>));
+    SET_SMEM((fused_kernel<10, MODE_GCM_SUM>));
+    SET_SMEM((fused_kernel<12, MODE_GCM_SUM>));
+    SET_SMEM((fused_kernel<14, MODE_GCM_SUM>));
 #undef SET_SMEM
     return cudaSuccess;
 }
@@ -1087,22 +1144,17 @@ cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t strea
         fused_kernel<14, MODE_GHASH><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
         return cudaGetLastError();
     }
-    const bool ctr = (mode == MODE_CTR);
+#define KF_LAUNCH(NRV)                                                                        \
+    if (mode == MODE_CTR) fused_kernel<NRV, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);         \
+    else if (mode == MODE_GCM_SUM) fused_kernel<NRV, MODE_GCM_SUM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p); \
+    else fused_kernel<NRV, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
     switch (nr) {
-    case 10:
-        if (ctr) fused_kernel<10, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        else fused_kernel<10, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        break;
-    case 12:
-        if (ctr) fused_kernel<12, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        else fused_kernel<12, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        break;
-    case 14:
-        if (ctr) fused_kernel<14, MODE_CTR><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        else fused_kernel<14, MODE_GCM><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
-        break;
+    case 10: KF_LAUNCH(10); break;
+    case 12: KF_LAUNCH(12); break;
+    case 14: KF_LAUNCH(14); break;
     default: return cudaErrorInvalidValue;
     }
+#undef KF_LAUNCH
     return cudaGetLastError();
 }
 

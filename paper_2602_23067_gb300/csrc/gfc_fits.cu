@@ -312,9 +312,12 @@ int fits_call(gcm_ctx *ctx, bool decrypt, const uint8_t *key, size_t key_len, co
     }
     uint8_t *tag_slot = (mem == GCM_MEM_DEVICE) ? buf + off_tag : nullptr;
     uint8_t host_tag[16];
+    uint32_t datasum = 0;
+    bool datasum_done = false;
     if (!decrypt) {
-        rc = gcm_encrypt(ctx, key, key_len, iv, 12, aad, aad_len, data_in, L.data_padded_bytes, data_out,
-                         mem == GCM_MEM_DEVICE ? tag_slot : host_tag, mem, stream);
+        rc = gcmgpu::ctx_run_with_datasum(ctx, key, key_len, iv, 12, aad, aad_len, data_in, L.data_padded_bytes, data_out,
+                                  mem == GCM_MEM_DEVICE ? tag_slot : host_tag, false, mem, stream, &datasum,
+                                  &datasum_done);
         if (rc == GCM_OK && mem == GCM_MEM_DEVICE) {
             cudaGetDevice(&prev);
             cudaSetDevice(ctx->device);
@@ -326,9 +329,12 @@ int fits_call(gcm_ctx *ctx, bool decrypt, const uint8_t *key, size_t key_len, co
         if (rc == GCM_OK) memcpy(tag_out, host_tag, 16);
     } else {
         memcpy(host_tag, tag_in, 16);
-        rc = gcm_decrypt_verify(ctx, key, key_len, iv, 12, aad, aad_len, data_in, L.data_padded_bytes,
-                                mem == GCM_MEM_DEVICE ? tag_slot : host_tag, data_out, mem, stream);
+        rc = gcmgpu::ctx_run_with_datasum(ctx, key, key_len, iv, 12, aad, aad_len, data_in, L.data_padded_bytes, data_out,
+                                  mem == GCM_MEM_DEVICE ? tag_slot : host_tag, true, mem, stream, &datasum,
+                                  &datasum_done);
     }
+    out->datasum = datasum;
+    out->datasum_valid = datasum_done ? 1 : 0;
     if (rc == GCM_ERR_AUTH)
         return set_result(out, rc, 2, "authentication tag mismatch: payload suppressed (data unit zero-filled)");
     if (rc != GCM_OK) {

@@ -48,6 +48,10 @@ def test_fits_roundtrip_header_aad(env, where, shape):
     d = ctx.fits_decrypt_verify(KEY, enc_in, IV, r.tag)
     back = bytes(d.data.cpu().numpy()) if where == "device" else d.data.tobytes()
     assert d.error_code == 0 and d.warning_code == 0 and back == f
+    # FITS DATASUM of the encrypted data unit, from the same pass, both ways
+    hdr_len = len(oracle.fits_split(f)[0])
+    ds = oracle.datasum(ref_enc[hdr_len:])
+    assert r.datasum == ds and d.datasum == ds
 
 
 def test_unpadded_input_is_zero_padded(env):
@@ -126,3 +130,17 @@ def test_rejects_multi_hdu_and_non_fits(env):
         ctx.fits_encrypt(KEY, f + bytes(2880), iv=IV)
     with pytest.raises(GcmError):
         ctx.fits_encrypt(KEY, b"\0" * 5760, iv=IV)
+
+
+def test_datasum_of_tampered_file_is_reported(env):
+    """The DATASUM is taken over the ciphertext as read, so a corrupted file
+    shows a DATASUM different from the stored one even though the tag check
+    (which rejects it) zero-fills the payload."""
+    torch, ctx = env
+    f = _file(12, 200, 100)
+    r = ctx.fits_encrypt(KEY, f, iv=IV)
+    enc = bytearray(r.data.tobytes())
+    enc[2880 + 123] ^= 0x10
+    d = ctx.fits_decrypt_verify(KEY, bytes(enc), IV, r.tag)
+    assert d.error_code == -3 and d.warning_code == 2
+    assert d.datasum == oracle.datasum(bytes(enc[2880:])) != r.datasum
