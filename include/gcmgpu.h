@@ -433,6 +433,47 @@ int gfc_fits_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                             const uint8_t *tag, int aad_mode, int mem, void *stream,
                             gfc_result *out);
 
+/* The paper's dual-key authenticated container (Sec. 3.2.2, Fig.
+ * "Structure of the Authenticated FITS Format").  gfc_container_encrypt turns
+ * a single-HDU FITS image into two HDUs:
+ *   HDU 0 (NAXIS = 0): NONCE_H, NONCE_D (12-byte nonces as lowercase hex),
+ *     AUTHTG_H, AUTHTG_D (the paper's AUTHTAG_H / AUTHTAG_D, shortened to the
+ *     8-character keyword limit; 16-byte tags as hex), ORIG_BPX, ORIG_NAX,
+ *     ORIG_NA1.. (the original BITPIX, NAXIS, NAXISn, abbreviated as in the
+ *     paper), and ENCHDR: the original header records encrypted with the
+ *     header key under NONCE_H (no AAD), as a hex long string (CONTINUE
+ *     cards of 64 characters).
+ *   HDU 1: a one-row binary table (TFORM1 = '<N>B', TTYPE1 = 'ENCDATA')
+ *     holding the N pixel bytes encrypted with the data key under NONCE_D
+ *     with AAD_D = NONCE_D || Serialize(ORIG_BITPIX) || Serialize(ORIG_NAXIS)
+ *     || Serialize(ORIG_NAXIS1) || ... (Sec. 3.2.3), and its DATASUM (from the
+ *     same pass; omitted on the staged host path).
+ * key_h/key_d: 16/24/32-byte keys (host).  nonce_h/nonce_d: 12 host bytes,
+ * or NULL to draw them from the operating system's entropy source.  fits is
+ * in the memory given by mem; out->data_buffer receives the container.
+ *
+ * gfc_decrypt_frame is the paper's gfc_decrypt_frame(ctx, file, key_h,
+ * key_d) (Table "Core functions"; Sec. 3.3.2 pipeline; Sec. 4.2 access
+ * behaviour).  key_h / key_d may be NULL (key not provisioned).  The output
+ * is always a structurally valid FITS file: the original header when key_h
+ * is given and AUTHTG_H verifies, else a minimal header from ORIG_* (header
+ * fallback, warning_code 1); the pixels when key_d is given and AUTHTG_D
+ * verifies over the pixels and the structural keywords, else zero bytes
+ * (payload suppression, warning_code 2, which takes precedence).  As in the
+ * paper, error_code is 0 in all of these cases; it is negative only for
+ * system errors or a malformed container.  out->datasum is the DATASUM of the
+ * stored (encrypted) table data, when the data key was used. */
+int gfc_container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len,
+                          const uint8_t *key_d, size_t key_d_len,
+                          const uint8_t *fits, size_t fits_len,
+                          const uint8_t *nonce_h, const uint8_t *nonce_d,
+                          int mem, void *stream, gfc_result *out);
+
+int gfc_decrypt_frame(gcm_ctx *ctx, const uint8_t *container, size_t len,
+                      const uint8_t *key_h, size_t key_h_len,
+                      const uint8_t *key_d, size_t key_d_len,
+                      int mem, void *stream, gfc_result *out);
+
 /* Releases out->data_buffer (mirrors the teardown side of the paper's API).
  * Safe on a zeroed or already released result. */
 void gfc_result_free(gcm_ctx *ctx, gfc_result *res);

@@ -116,6 +116,10 @@ SIGNATURES = {
     "gfc_fits_decrypt_verify": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, ctypes.c_int,
                                                _VP, ctypes.POINTER(GfcResult)]),
     "gfc_result_free": (None, [_VP, ctypes.POINTER(GfcResult)]),
+    "gfc_container_encrypt": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP, ctypes.c_int, _VP,
+                                             ctypes.POINTER(GfcResult)]),
+    "gfc_decrypt_frame": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, ctypes.c_int, _VP,
+                                         ctypes.POINTER(GfcResult)]),
     "gcm_noalloc_last_error": (ctypes.c_char_p, []),
 }
 

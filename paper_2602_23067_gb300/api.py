@@ -337,6 +337,62 @@ class Context:
         return FitsResult(data, rc, warning, msg, iv_out.raw if not decrypt else bytes(iv),
                           tag_out.raw if not decrypt else bytes(tag), datasum)
 
+    def _take_result(self, rc, res, device, like):
+        import numpy as np
+
+        msg = res.error_message.decode("utf-8", "replace")
+        data = None
+        if res.data_buffer:
+            n = res.buffer_size
+            if device:
+                data = _dev_tensor_copy(res.data_buffer, n, like.device)
+            else:
+                data = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(res.data_buffer)).copy()
+        datasum = int(res.datasum) if res.datasum_valid else None
+        warning = res.warning_code
+        if res.data_buffer:
+            lib.gfc_result_free(self.handle, ctypes.byref(res))
+        if rc != GCM_OK:
+            raise GcmError(rc, msg)
+        return FitsResult(data, rc, warning, msg, datasum=datasum)
+
+    def container_encrypt(self, key_h: bytes, key_d: bytes, fits, nonce_h: Optional[bytes] = None,
+                          nonce_d: Optional[bytes] = None, stream=None) -> "FitsResult":
+        """gfc_container_encrypt: the paper's two-HDU dual-key container of a
+        FITS image (bytes/numpy on the host or a CUDA uint8 tensor)."""
+        device = hasattr(fits, "is_cuda") and fits.is_cuda
+        if device:
+            fp, fl = _dev_buf(fits)
+            mem, st = GCM_MEM_DEVICE, _stream_handle(stream)
+        else:
+            fp, fl, fk = _host_buf(fits)
+            mem, st = GCM_MEM_HOST, (stream or 0)
+        hp, hl, hk = _host_buf(key_h)
+        dp, dl, dk = _host_buf(key_d)
+        nh = ctypes.create_string_buffer(bytes(nonce_h), 12) if nonce_h is not None else None
+        nd = ctypes.create_string_buffer(bytes(nonce_d), 12) if nonce_d is not None else None
+        res = GfcResult()
+        rc = lib.gfc_container_encrypt(self.handle, hp, hl, dp, dl, fp, fl,
+                                       ctypes.addressof(nh) if nh is not None else None,
+                                       ctypes.addressof(nd) if nd is not None else None, mem, st, ctypes.byref(res))
+        return self._take_result(rc, res, device, fits)
+
+    def decrypt_frame(self, container, key_h: Optional[bytes], key_d: Optional[bytes], stream=None) -> "FitsResult":
+        """gfc_decrypt_frame: the FITS file of a container, with the paper's
+        warning codes (0 full access, 1 header fallback, 2 payload suppressed)."""
+        device = hasattr(container, "is_cuda") and container.is_cuda
+        if device:
+            cp, cl = _dev_buf(container)
+            mem, st = GCM_MEM_DEVICE, _stream_handle(stream)
+        else:
+            cp, cl, ck = _host_buf(container)
+            mem, st = GCM_MEM_HOST, (stream or 0)
+        hp, hl, hk = _host_buf(key_h) if key_h is not None else (None, 0, None)
+        dp, dl, dk = _host_buf(key_d) if key_d is not None else (None, 0, None)
+        res = GfcResult()
+        rc = lib.gfc_decrypt_frame(self.handle, cp, cl, hp, hl, dp, dl, mem, st, ctypes.byref(res))
+        return self._take_result(rc, res, device, container)
+
     def fits_encrypt_raw(self, key: bytes, fits, iv: bytes, aad_mode: int = GFC_AAD_HEADER, stream=None):
         """gfc_fits_encrypt on a CUDA tensor without copying the result: returns
         (GfcResult, tag).  The result buffer belongs to the library until

@@ -13,8 +13,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <sys/random.h>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -345,6 +347,451 @@ int fits_call(gcm_ctx *ctx, bool decrypt, const uint8_t *key, size_t key_len, co
     return set_result(out, GCM_OK, 0, "");
 }
 
+// ---------------------------------------------------------------------
+// The paper's dual-key container (Sec. 3.2.2): HDU 0 holds the nonces, the
+// two tags, the ORIG_* structural keywords and ENCHDR (the original header
+// encrypted with the header key); HDU 1 is a one-row binary table whose
+// single column holds the pixel bytes encrypted with the data key, with
+// AAD_D = NONCE_D || Serialize(ORIG_BITPIX) || Serialize(ORIG_NAXIS) || ...
+// Encodings where the paper is silent: nonces and tags as lowercase hex
+// strings, the tag keywords shortened to AUTHTG_H / AUTHTG_D (eight
+// characters), ENCHDR as a lowercase hex long string of 64 characters per
+// card (CONTINUE convention), ENCHDR authenticated without AAD.
+// ---------------------------------------------------------------------
+std::string pad80(const std::string &t) { return t + std::string(CARD - t.size(), ' '); }
+
+std::string kcard_int(const char *key, int64_t v)
+{
+    char b[96];
+    snprintf(b, sizeof(b), "%-8s= %20lld", key, (long long)v);
+    return pad80(b);
+}
+
+std::string kcard_logical(const char *key, bool v)
+{
+    char b[96];
+    snprintf(b, sizeof(b), "%-8s= %20s", key, v ? "T" : "F");
+    return pad80(b);
+}
+
+std::string kcard_str(const char *key, const std::string &v)
+{
+    std::string t = v;
+    if (t.size() < 8) t += std::string(8 - t.size(), ' ');
+    char b[96];
+    snprintf(b, sizeof(b), "%-8s= '%s'", key, t.c_str());
+    return pad80(b);
+}
+
+std::string hexs(const uint8_t *p, size_t n)
+{
+    static const char *d = "0123456789abcdef";
+    std::string s(2 * n, '0');
+    for (size_t i = 0; i < n; i++) {
+        s[2 * i] = d[p[i] >> 4];
+        s[2 * i + 1] = d[p[i] & 15];
+    }
+    return s;
+}
+
+bool unhex(const std::string &s, std::string *out)
+{
+    if (s.size() % 2) return false;
+    out->assign(s.size() / 2, '\0');
+    for (size_t i = 0; i < s.size(); i += 2) {
+        int v = 0;
+        for (int k = 0; k < 2; k++) {
+            const char c = s[i + k];
+            const int x = (c >= '0' && c <= '9') ? c - '0' : (c >= 'a' && c <= 'f') ? c - 'a' + 10 : -1;
+            if (x < 0) return false;
+            v = v * 16 + x;
+        }
+        (*out)[i / 2] = (char)v;
+    }
+    return true;
+}
+
+// Cards + END, blank-filled to whole records.
+std::string header_records(const std::vector<std::string> &cards)
+{
+    std::string h;
+    for (const auto &c : cards) h += c;
+    h += pad80("END");
+    h += std::string((REC - h.size() % REC) % REC, ' ');
+    return h;
+}
+
+size_t header_records_size(size_t n_cards) { return ((n_cards + 1) * CARD + REC - 1) / REC * REC; }
+
+constexpr size_t HEX_PER_CARD = 64;
+
+// Keyword -> value text (strings unquoted and right-trimmed, long strings
+// joined over CONTINUE cards, comments dropped) of the header at hdr.
+std::map<std::string, std::string> header_keys(const std::string &hdr)
+{
+    std::map<std::string, std::string> k;
+    std::string last;
+    for (size_t off = 0; off + CARD <= hdr.size(); off += CARD) {
+        const std::string card = hdr.substr(off, CARD);
+        const std::string name = keyword(reinterpret_cast<const uint8_t *>(card.data()));
+        if (name == "END") break;
+        if (name == "CONTINUE" && !last.empty()) {
+            const size_t q0 = card.find('\''), q1 = card.rfind('\'');
+            std::string &v = k[last];
+            if (q0 != std::string::npos && q1 > q0 && !v.empty() && v.back() == '&') {
+                v.pop_back();
+                v += card.substr(q0 + 1, q1 - q0 - 1);
+            }
+            continue;
+        }
+        if (card.compare(8, 2, "= ") != 0) {
+            last.clear();
+            continue;
+        }
+        std::string v = card.substr(10);
+        const size_t a = v.find_first_not_of(' ');
+        v = (a == std::string::npos) ? "" : v.substr(a);
+        if (!v.empty() && v[0] == '\'') {
+            const size_t q1 = v.rfind('\'');
+            v = v.substr(1, q1 > 0 ? q1 - 1 : 0);
+            while (!v.empty() && v.back() == ' ') v.pop_back();
+        } else {
+            const size_t sl = v.find('/');
+            if (sl != std::string::npos) v = v.substr(0, sl);
+            while (!v.empty() && v.back() == ' ') v.pop_back();
+        }
+        k[name] = v;
+        last = name;
+    }
+    return k;
+}
+
+bool key_int(const std::map<std::string, std::string> &k, const std::string &name, int64_t *v)
+{
+    auto it = k.find(name);
+    if (it == k.end() || it->second.empty()) return false;
+    char *end = nullptr;
+    const long long x = strtoll(it->second.c_str(), &end, 10);
+    if (*end) return false;
+    *v = x;
+    return true;
+}
+
+bool check_key(const uint8_t *key, size_t key_len)
+{
+    return key && (key_len == 16 || key_len == 24 || key_len == 32);
+}
+
+// Copies host bytes into the result buffer (device or pinned host).
+cudaError_t put_bytes(uint8_t *dst, const void *src, size_t n, int mem, cudaStream_t s)
+{
+    if (!n) return cudaSuccess;
+    if (mem == GCM_MEM_DEVICE) return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, s);
+    memcpy(dst, src, n);
+    return cudaSuccess;
+}
+
+cudaError_t zero_bytes(uint8_t *dst, size_t n, int mem, cudaStream_t s)
+{
+    if (!n) return cudaSuccess;
+    if (mem == GCM_MEM_DEVICE) return cudaMemsetAsync(dst, 0, n, s);
+    memset(dst, 0, n);
+    return cudaSuccess;
+}
+
+struct DevSel {
+    int prev = -1;
+    explicit DevSel(int d)
+    {
+        cudaGetDevice(&prev);
+        cudaSetDevice(d);
+    }
+    ~DevSel()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+int container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, const uint8_t *key_d, size_t key_d_len,
+                      const uint8_t *fits, size_t fits_len, const uint8_t *nonce_h_in, const uint8_t *nonce_d_in,
+                      int mem, void *stream, gfc_result *out)
+{
+    if (!out) return GCM_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->mem = mem;
+    out->stream = stream;
+    if (!ctx || !fits) return set_result(out, GCM_ERR_INVALID_ARG, 0, "context or input is NULL");
+    if (!check_key(key_h, key_h_len) || !check_key(key_d, key_d_len))
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "header and data keys must be 16, 24 or 32 bytes");
+    if (mem != GCM_MEM_DEVICE && mem != GCM_MEM_HOST)
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");
+    if (mem == GCM_MEM_DEVICE && ((uintptr_t)fits & 15u))
+        return set_result(out, GCM_ERR_ALIGNMENT, 0, "device FITS buffer must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevSel sel(ctx->device);
+    std::string err, hdr_s;
+    int rc;
+    if (mem == GCM_MEM_DEVICE) {
+        rc = read_device_header(fits, fits_len, s, &hdr_s, &err);
+        if (rc) return set_result(out, rc, 0, err.c_str());
+    } else {
+        gfc_layout L0;
+        rc = parse_layout(fits, fits_len, &L0, &err);
+        if (rc) return set_result(out, rc, 0, err.c_str());
+        hdr_s.assign(reinterpret_cast<const char *>(fits), L0.header_bytes);
+    }
+    gfc_layout L;
+    rc = parse_layout(reinterpret_cast<const uint8_t *>(hdr_s.data()), hdr_s.size(), &L, &err);
+    if (rc) return set_result(out, rc, 0, err.c_str());
+    hdr_s.resize(L.header_bytes);
+    if (fits_len < L.header_bytes + L.data_bytes)
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "file shorter than its data unit");
+    if (fits_len > L.header_bytes + L.data_padded_bytes)
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "bytes after the primary data unit (only single-HDU files)");
+    if (L.naxis > 9) return set_result(out, GCM_ERR_INVALID_ARG, 0, "at most 9 axes (ORIG_NA1..ORIG_NA9)");
+
+    uint8_t nonce_h[12], nonce_d[12];
+    if (nonce_h_in) memcpy(nonce_h, nonce_h_in, 12);
+    if (nonce_d_in) memcpy(nonce_d, nonce_d_in, 12);
+    if ((!nonce_h_in && getrandom(nonce_h, 12, 0) != 12) || (!nonce_d_in && getrandom(nonce_d, 12, 0) != 12))
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "getrandom failed");
+
+    // ENCHDR: the header records under the header key (host memory, small).
+    std::string enchdr(hdr_s.size(), '\0');
+    uint8_t tag_h[16];
+    rc = gcm_encrypt(ctx, key_h, key_h_len, nonce_h, 12, nullptr, 0, reinterpret_cast<const uint8_t *>(hdr_s.data()),
+                     hdr_s.size(), reinterpret_cast<uint8_t *>(&enchdr[0]), tag_h, GCM_MEM_HOST, nullptr);
+    if (rc) return set_result(out, rc, 0, gcm_last_error());
+
+    // Layout of the container.
+    const std::string hx = hexs(reinterpret_cast<const uint8_t *>(enchdr.data()), enchdr.size());
+    const size_t n_hex_cards = (hx.size() + HEX_PER_CARD - 1) / HEX_PER_CARD;
+    const size_t prim_cards = 10 + (size_t)L.naxis + (n_hex_cards ? n_hex_cards : 1);
+    const size_t prim_bytes = header_records_size(prim_cards);
+    const size_t ext_bytes = header_records_size(11);
+    const size_t N = L.data_bytes;
+    const size_t blob_off = prim_bytes + ext_bytes;
+    const size_t total = blob_off + (N + REC - 1) / REC * REC;
+    const std::string aad = structural_aad(nonce_d, L, reinterpret_cast<const uint8_t *>(hdr_s.data()), hdr_s.size());
+    const size_t off_aad = (total + 255) / 256 * 256;
+    const size_t off_tag = (off_aad + aad.size() + 255) / 256 * 256;
+    const size_t alloc = off_tag + 256;
+    uint8_t *buf = nullptr;
+    cudaError_t e = (mem == GCM_MEM_DEVICE)
+                        ? cudaMallocFromPoolAsync(reinterpret_cast<void **>(&buf), alloc, ctx->pool, s)
+                        : cudaMallocHost(reinterpret_cast<void **>(&buf), alloc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_result(out, GCM_ERR_NO_MEMORY, 0, "cannot allocate the result buffer");
+    }
+    out->data_buffer = buf;
+    out->buffer_size = total;
+
+    // Pixels under the data key with AAD_D, straight into the table's data
+    // unit; the DATASUM of the ciphertext comes from the same pass.
+    const uint8_t *aad_p = reinterpret_cast<const uint8_t *>(aad.data());
+    if (mem == GCM_MEM_DEVICE) {
+        e = put_bytes(buf + off_aad, aad.data(), aad.size(), mem, s);
+        aad_p = buf + off_aad;
+    }
+    if (e == cudaSuccess) e = zero_bytes(buf + blob_off + N, total - blob_off - N, mem, s);
+    if (e != cudaSuccess) {
+        gfc_result_free(ctx, out);
+        return set_result(out, GCM_ERR_CUDA, 0, cudaGetErrorString(e));
+    }
+    uint8_t tag_d[16];
+    uint8_t *tag_slot = (mem == GCM_MEM_DEVICE) ? buf + off_tag : tag_d;
+    uint32_t dsum = 0;
+    bool dsum_done = false;
+    rc = gcmgpu::ctx_run_with_datasum(ctx, key_d, key_d_len, nonce_d, 12, aad_p, aad.size(), fits + L.header_bytes, N,
+                                      buf + blob_off, tag_slot, false, mem, stream, &dsum, &dsum_done);
+    if (rc == GCM_OK && mem == GCM_MEM_DEVICE) {
+        e = cudaMemcpyAsync(tag_d, tag_slot, 16, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = GCM_ERR_CUDA;
+    }
+    if (rc != GCM_OK) {
+        std::string m = gcm_last_error();
+        gfc_result_free(ctx, out);
+        return set_result(out, rc, 0, m.c_str());
+    }
+
+    // The two headers, now that both tags are known.
+    std::vector<std::string> pc = {kcard_logical("SIMPLE", true), kcard_int("BITPIX", 8), kcard_int("NAXIS", 0),
+                                   kcard_logical("EXTEND", true), kcard_str("NONCE_H", hexs(nonce_h, 12)),
+                                   kcard_str("NONCE_D", hexs(nonce_d, 12)), kcard_str("AUTHTG_H", hexs(tag_h, 16)),
+                                   kcard_str("AUTHTG_D", hexs(tag_d, 16)), kcard_int("ORIG_BPX", L.bitpix),
+                                   kcard_int("ORIG_NAX", L.naxis)};
+    for (int i = 1; i <= L.naxis; i++) {
+        const std::string name = "ORIG_NA" + std::to_string(i);
+        pc.push_back(kcard_int(name.c_str(), L.naxes[i - 1]));
+    }
+    for (size_t i = 0; i < (n_hex_cards ? n_hex_cards : 1); i++) {
+        const std::string part = hx.substr(i * HEX_PER_CARD, HEX_PER_CARD);
+        const std::string amp = (i + 1 < n_hex_cards) ? "&" : "";
+        pc.push_back(pad80(i == 0 ? std::string("ENCHDR  = '") + part + amp + "'"
+                                  : std::string("CONTINUE  '") + part + amp + "'"));
+    }
+    const std::string prim = header_records(pc);
+    std::vector<std::string> xc = {kcard_str("XTENSION", "BINTABLE"), kcard_int("BITPIX", 8), kcard_int("NAXIS", 2),
+                                   kcard_int("NAXIS1", (int64_t)N), kcard_int("NAXIS2", 1), kcard_int("PCOUNT", 0),
+                                   kcard_int("GCOUNT", 1), kcard_int("TFIELDS", 1), kcard_str("TTYPE1", "ENCDATA"),
+                                   kcard_str("TFORM1", std::to_string(N) + "B")};
+    if (dsum_done) xc.push_back(kcard_str("DATASUM", std::to_string(dsum)));  // omitted when not computed
+    const std::string ext = header_records(xc);
+    e = put_bytes(buf, prim.data(), prim.size(), mem, s);
+    if (e == cudaSuccess) e = put_bytes(buf + prim_bytes, ext.data(), ext.size(), mem, s);
+    if (e == cudaSuccess && mem == GCM_MEM_DEVICE) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        gfc_result_free(ctx, out);
+        return set_result(out, GCM_ERR_CUDA, 0, cudaGetErrorString(e));
+    }
+    out->datasum = dsum;
+    out->datasum_valid = dsum_done ? 1 : 0;
+    return set_result(out, GCM_OK, 0, "");
+}
+
+int decrypt_frame(gcm_ctx *ctx, const uint8_t *cont, size_t len, const uint8_t *key_h, size_t key_h_len,
+                  const uint8_t *key_d, size_t key_d_len, int mem, void *stream, gfc_result *out)
+{
+    if (!out) return GCM_ERR_INVALID_ARG;
+    memset(out, 0, sizeof(*out));
+    out->mem = mem;
+    out->stream = stream;
+    if (!ctx || !cont) return set_result(out, GCM_ERR_INVALID_ARG, 0, "context or input is NULL");
+    if ((key_h && !check_key(key_h, key_h_len)) || (key_d && !check_key(key_d, key_d_len)))
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "keys must be 16, 24 or 32 bytes (or NULL: not provisioned)");
+    if (mem != GCM_MEM_DEVICE && mem != GCM_MEM_HOST)
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "mem must be GCM_MEM_DEVICE or GCM_MEM_HOST");
+    if (mem == GCM_MEM_DEVICE && ((uintptr_t)cont & 15u))
+        return set_result(out, GCM_ERR_ALIGNMENT, 0, "device container buffer must be 16-byte aligned");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DevSel sel(ctx->device);
+    std::string err, prim, ext;
+    int rc;
+    // The two headers (host copies).
+    auto read_hdr = [&](size_t off, std::string *h) -> int {
+        if (off >= len) return GCM_ERR_INVALID_ARG;
+        if (mem == GCM_MEM_DEVICE) return read_device_header(cont + off, len - off, s, h, &err);
+        h->clear();
+        for (size_t o = off; o + REC <= len; o += REC) {
+            h->append(reinterpret_cast<const char *>(cont + o), REC);
+            for (size_t c = 0; c < REC; c += CARD)
+                if (keyword(cont + o + c) == "END") return GCM_OK;
+        }
+        err = "no END card";
+        return GCM_ERR_INVALID_ARG;
+    };
+    rc = read_hdr(0, &prim);
+    if (rc == GCM_OK) rc = read_hdr(prim.size(), &ext);
+    if (rc) return set_result(out, rc, 0, err.empty() ? "not a container" : err.c_str());
+    const auto P = header_keys(prim), X = header_keys(ext);
+    int64_t n = 0, bitpix = 0, naxis = -1;
+    std::string nonce_h, nonce_d, tag_h, tag_d, enchdr;
+    const auto str = [](const std::map<std::string, std::string> &k, const char *name) {
+        auto it = k.find(name);
+        return it == k.end() ? std::string() : it->second;
+    };
+    if (str(X, "XTENSION") != "BINTABLE" || !key_int(X, "NAXIS1", &n) || n < 0 ||
+        !unhex(str(P, "NONCE_H"), &nonce_h) || nonce_h.size() != 12 || !unhex(str(P, "NONCE_D"), &nonce_d) ||
+        nonce_d.size() != 12 || !unhex(str(P, "AUTHTG_H"), &tag_h) || tag_h.size() != 16 ||
+        !unhex(str(P, "AUTHTG_D"), &tag_d) || tag_d.size() != 16 || !key_int(P, "ORIG_BPX", &bitpix) ||
+        !key_int(P, "ORIG_NAX", &naxis) || naxis < 0 || naxis > 9 || !unhex(str(P, "ENCHDR"), &enchdr))
+        return set_result(out, GCM_ERR_INVALID_ARG, 0, "missing or malformed container keywords");
+    gfc_layout L;
+    memset(&L, 0, sizeof(L));
+    L.bitpix = (int)bitpix;
+    L.naxis = (int)naxis;
+    for (int i = 1; i <= naxis; i++) {
+        int64_t v;
+        if (!key_int(P, ("ORIG_NA" + std::to_string(i)).c_str(), &v) || v < 0)
+            return set_result(out, GCM_ERR_INVALID_ARG, 0, "missing ORIG_NAn");
+        L.naxes[i - 1] = v;
+    }
+    const size_t blob_off = prim.size() + ext.size();
+    if (blob_off + (size_t)n > len) return set_result(out, GCM_ERR_INVALID_ARG, 0, "container shorter than its table");
+
+    // Header: ENCHDR under the header key, else the fallback from ORIG_*.
+    int warning = 0;
+    std::string header;
+    if (key_h && !enchdr.empty() && enchdr.size() % REC == 0) {
+        std::string h(enchdr.size(), '\0');
+        rc = gcm_decrypt_verify(ctx, key_h, key_h_len, reinterpret_cast<const uint8_t *>(nonce_h.data()), 12, nullptr,
+                                0, reinterpret_cast<const uint8_t *>(enchdr.data()), enchdr.size(),
+                                reinterpret_cast<const uint8_t *>(tag_h.data()), reinterpret_cast<uint8_t *>(&h[0]),
+                                GCM_MEM_HOST, nullptr);
+        if (rc == GCM_OK) header = h;
+        else if (rc != GCM_ERR_AUTH) return set_result(out, rc, 0, gcm_last_error());
+    }
+    if (header.empty()) {
+        std::vector<std::string> c = {kcard_logical("SIMPLE", true), kcard_int("BITPIX", bitpix),
+                                      kcard_int("NAXIS", naxis)};
+        for (int i = 1; i <= naxis; i++)
+            c.push_back(kcard_int(("NAXIS" + std::to_string(i)).c_str(), L.naxes[i - 1]));
+        header = header_records(c);
+        warning = 1;
+    }
+    const size_t total = header.size() + ((size_t)n + REC - 1) / REC * REC;
+    const std::string aad = structural_aad(reinterpret_cast<const uint8_t *>(nonce_d.data()), L, nullptr, 0);
+    const size_t off_aad = (total + 255) / 256 * 256;
+    const size_t off_tag = (off_aad + aad.size() + 255) / 256 * 256;
+    const size_t alloc = off_tag + 256;
+    uint8_t *buf = nullptr;
+    cudaError_t e = (mem == GCM_MEM_DEVICE)
+                        ? cudaMallocFromPoolAsync(reinterpret_cast<void **>(&buf), alloc, ctx->pool, s)
+                        : cudaMallocHost(reinterpret_cast<void **>(&buf), alloc);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_result(out, GCM_ERR_NO_MEMORY, 0, "cannot allocate the result buffer");
+    }
+    out->data_buffer = buf;
+    out->buffer_size = total;
+    e = put_bytes(buf, header.data(), header.size(), mem, s);
+    if (e == cudaSuccess) e = zero_bytes(buf + header.size() + n, total - header.size() - n, mem, s);
+    const uint8_t *aad_p = reinterpret_cast<const uint8_t *>(aad.data());
+    uint8_t *tag_p = reinterpret_cast<uint8_t *>(&tag_d[0]);
+    if (e == cudaSuccess && mem == GCM_MEM_DEVICE) {
+        e = put_bytes(buf + off_aad, aad.data(), aad.size(), mem, s);
+        if (e == cudaSuccess) e = put_bytes(buf + off_tag, tag_d.data(), 16, mem, s);
+        aad_p = buf + off_aad;
+        tag_p = buf + off_tag;
+    }
+    if (e != cudaSuccess) {
+        gfc_result_free(ctx, out);
+        return set_result(out, GCM_ERR_CUDA, 0, cudaGetErrorString(e));
+    }
+    // Pixels: decrypted and verified under the data key (zero-filled by the
+    // library on a tag mismatch), or suppressed without one.
+    bool data_ok = false;
+    uint32_t dsum = 0;
+    bool dsum_done = false;
+    if (key_d) {
+        rc = gcmgpu::ctx_run_with_datasum(ctx, key_d, key_d_len, reinterpret_cast<const uint8_t *>(nonce_d.data()), 12,
+                                          aad_p, aad.size(), cont + blob_off, (size_t)n, buf + header.size(), tag_p,
+                                          true, mem, stream, &dsum, &dsum_done);
+        if (rc == GCM_OK) data_ok = true;
+        else if (rc != GCM_ERR_AUTH) {
+            std::string m = gcm_last_error();
+            gfc_result_free(ctx, out);
+            return set_result(out, rc, 0, m.c_str());
+        }
+    } else {
+        e = zero_bytes(buf + header.size(), (size_t)n, mem, s);
+        if (e == cudaSuccess && mem == GCM_MEM_DEVICE) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            gfc_result_free(ctx, out);
+            return set_result(out, GCM_ERR_CUDA, 0, cudaGetErrorString(e));
+        }
+    }
+    if (mem == GCM_MEM_DEVICE) cudaStreamSynchronize(s);
+    if (!data_ok) warning = 2;
+    out->datasum = dsum;
+    out->datasum_valid = dsum_done ? 1 : 0;
+    return set_result(out, GCM_OK, warning,
+                      warning == 2 ? "payload suppressed (data key missing or tag mismatch)"
+                                   : warning == 1 ? "header fallback (header key missing or tag mismatch)" : "");
+}
+
 }  // namespace
 
 extern "C" {
@@ -370,6 +817,20 @@ int gfc_fits_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len, co
 {
     return fits_call(ctx, true, key, key_len, fits_enc, len, iv12, nullptr, tag, nullptr, aad_mode, mem, stream,
                      out);
+}
+
+int gfc_container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, const uint8_t *key_d,
+                          size_t key_d_len, const uint8_t *fits, size_t fits_len, const uint8_t *nonce_h,
+                          const uint8_t *nonce_d, int mem, void *stream, gfc_result *out)
+{
+    return container_encrypt(ctx, key_h, key_h_len, key_d, key_d_len, fits, fits_len, nonce_h, nonce_d, mem, stream,
+                             out);
+}
+
+int gfc_decrypt_frame(gcm_ctx *ctx, const uint8_t *container, size_t len, const uint8_t *key_h, size_t key_h_len,
+                      const uint8_t *key_d, size_t key_d_len, int mem, void *stream, gfc_result *out)
+{
+    return decrypt_frame(ctx, container, len, key_h, key_h_len, key_d, key_d_len, mem, stream, out);
 }
 
 void gfc_result_free(gcm_ctx *ctx, gfc_result *res)
