@@ -464,9 +464,9 @@ struct GroupCache {
 };
 
 // One tile: Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C
-// are aligned to its end (the first tile is the short one and is treated as
-// left-padded with zero blocks).  Warp w owns segment w of the tile
-// (S = tile/16 blocks).  On whole-payload segments the warp walks windows
+// are aligned to its end (the first tile is the short one; it is treated as
+// the smallest tile of 2^lg >= its length blocks, left-padded with zero
+// blocks).  Warp w owns segment w of the tile (S = 2^lg/16 blocks).  On whole-payload segments the warp walks windows
 // of 32 counters aligned to multiples of 32, so a window never crosses a
 // 256-counter group: rounds 1 and 2 of AES then need only the lookups that
 // depend on the counter's low byte (counter-mode caching; the rest are
@@ -488,10 +488,15 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     const KeyMat *km = v.km;
     const gf128 *segf = reinterpret_cast<const gf128 *>(smem + SM_SEGF);
     gf128 *red = reinterpret_cast<gf128 *>(smem + SM_RED);
-    const int64_t seg_blocks = (int64_t)1 << (v.tile_log2 - KF_LOG2_WARPS);
-
     const int64_t tend = (int64_t)v.M - (int64_t)((v.K - 1 - tile) << v.tile_log2);
-    const int64_t tv_lo = tend - ((int64_t)1 << v.tile_log2);
+    // The first tile is the short one.  It is laid out as the smallest tile
+    // size 2^lg (lg >= SEGF_MIN_LOG2) that holds it, so that all warps share
+    // its blocks; its end, and so its partial, is the same at any size.
+    uint32_t lg = v.tile_log2;
+    if (tile == 0)
+        while (lg > (uint32_t)SEGF_MIN_LOG2 && ((int64_t)1 << (lg - 1)) >= tend) lg--;
+    const int64_t seg_blocks = (int64_t)1 << (lg - KF_LOG2_WARPS);
+    const int64_t tv_lo = tend - ((int64_t)1 << lg);
     const int64_t seg_hi = tv_lo + (int64_t)(warp + 1) * seg_blocks;
     int64_t seg_lo = tv_lo + (int64_t)warp * seg_blocks;
     if (seg_lo < 0) seg_lo = 0;
@@ -637,8 +642,17 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
         for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
     // Every lane holds the warp's sum z; the whole warp multiplies it by the
     // segment factor (warp-uniform branch).
-    if (warp != KF_WARPS - 1)
-        z = gf_mul_warp(z, segf[warp], reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
+    if (warp != KF_WARPS - 1) {
+        gf128 f;
+        if (lg == v.tile_log2) {
+            f = segf[warp];
+        } else {
+            const gf128 *g = &km->segf[lg - SEGF_MIN_LOG2][warp];
+#pragma unroll
+            for (int k = 0; k < 4; k++) f.w[k] = __ldg(&g->w[k]);
+        }
+        z = gf_mul_warp(z, f, reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
+    }
     if (lane == 0) red[warp] = z;
     uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
     if (MODE == MODE_GCM_SUM) {
@@ -709,7 +723,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
 // KB: many messages in one persistent launch
 // ---------------------------------------------------------------------
 template <int NR>
-__device__ __noinline__ void batch_tile(uint8_t *smem, const MsgView &v, const LaneConst &L, uint64_t tile,
+__device__ __forceinline__ void batch_tile(uint8_t *smem, const MsgView &v, const LaneConst &L, uint64_t tile,
                                         GroupCache &gc)
 {
     const uint8_t *t01 = smem + SM_T01;
@@ -800,18 +814,27 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
     GroupCache gc;
     for (;;) {
         __syncthreads();  // previous item (and its tables) fully done
-        if (threadIdx.x == 0) {
-            const uint64_t item = atomicAdd(p.item_counter, 1ull);
-            s_item = item;
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            uint64_t item = 0;
+            if (lane == 0) item = atomicAdd(p.item_counter, 1ull);
+            item = __shfl_sync(0xFFFFFFFFu, item, 0);
+            if (lane == 0) s_item = item;
             if (item < p.total_items) {
-                // The message whose item range holds `item` (item_base is sorted).
+                // The message whose item range holds `item` (item_base is
+                // strictly increasing): a 32-way search, each lane probing one
+                // point of the range, so 10^4 messages take 3 rounds.
                 uint32_t lo = 0, hi = p.n - 1;
                 while (lo < hi) {
-                    const uint32_t mid = (lo + hi + 1) / 2;
-                    if (p.msgs[mid].item_base <= item) lo = mid;
-                    else hi = mid - 1;
+                    const uint32_t step = (hi - lo) / 32 + 1;
+                    const uint64_t probe = (uint64_t)lo + (uint64_t)(lane + 1) * step;
+                    const bool le = probe <= hi && p.msgs[probe].item_base <= item;
+                    const uint32_t c = (uint32_t)__popc(__ballot_sync(0xFFFFFFFFu, le));
+                    const uint64_t nhi = (uint64_t)lo + (uint64_t)(c + 1) * step - 1;
+                    lo += c * step;
+                    hi = nhi < hi ? (uint32_t)nhi : hi;
                 }
-                s_msg = lo;
+                if (lane == 0) s_msg = lo;
             }
         }
         __syncthreads();
