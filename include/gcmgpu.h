@@ -133,6 +133,24 @@ int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
  * returns to the default. */
 int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2);
 
+/* AES engine of the single-message device pass (gcm_encrypt,
+ * gcm_decrypt_verify, gcm_ctr_xor, the FITS calls).  The paper builds on a
+ * bit-sliced AES-CTR core (Sec. 5.2, citing Lee et al. 2024); this library
+ * defaults to round tables in shared memory and offers the bit-sliced form:
+ *   GCM_AES_TABLES    (0, default) T-table rounds, one block per lane, with
+ *                     counter-mode caching of rounds 1-2;
+ *   GCM_AES_BITSLICED (1) 32 counter blocks per thread as 128 bitsliced words
+ *                     (the S-box as a 129-gate AND/XOR circuit derived from
+ *                     the tower field GF(((2^2)^2)^2)), 256 threads per SM.
+ * Ciphertexts and tags are identical; only speed differs.  GHASH uses the
+ * same shared-memory table in both.  Segments that touch the AAD or a final
+ * partial block, the GHASH-only pass, gcm_batch, the staged host-memory
+ * pipeline and gcm_encrypt_noalloc always use the tables.
+ * Returns GCM_ERR_INVALID_ARG for another value. */
+#define GCM_AES_TABLES 0
+#define GCM_AES_BITSLICED 1
+int gcm_ctx_set_aes_impl(gcm_ctx *ctx, int impl);
+
 /* Autotuner (the analogue of the paper's per-GPU (TS, R) search, Sec. 5.3,
  * Table "Kernel-optimal parameters"): times a GCM encryption of
  * 16 KiB, 64 KiB, 256 KiB, ... (x4) up to max_bytes (at most 1 GiB) of

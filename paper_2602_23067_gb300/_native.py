@@ -25,6 +25,8 @@ GCM_ERR_BUSY = -8
 
 GCM_MEM_DEVICE = 0
 GCM_MEM_HOST = 1
+GCM_AES_TABLES = 0
+GCM_AES_BITSLICED = 1
 
 STATUS_NAMES = {
     GCM_OK: "GCM_OK",
@@ -90,6 +92,7 @@ SIGNATURES = {
     "gcm_sync": (ctypes.c_int, [_VP, _VP]),
     "gcm_ctx_set_key_cache": (ctypes.c_int, [_VP, _SZ]),
     "gcm_ctx_set_tile_log2": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "gcm_ctx_set_aes_impl": (ctypes.c_int, [_VP, ctypes.c_int]),
     "gcm_ctx_autotune": (ctypes.c_int, [_VP, _SZ, _SZ, _VP]),
     "gcm_ctx_set_tuning": (ctypes.c_int, [_VP, _VP]),
     "gcm_ctr_xor": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, _VP, _VP]),

@@ -152,6 +152,10 @@ class Context:
         """gcm_ctx_set_tile_log2: force tiles of 2^tile_log2 blocks (0 = default)."""
         check(lib.gcm_ctx_set_tile_log2(self.handle, tile_log2))
 
+    def set_aes_impl(self, impl: int) -> None:
+        """gcm_ctx_set_aes_impl: GCM_AES_TABLES (0) or GCM_AES_BITSLICED (1)."""
+        check(lib.gcm_ctx_set_aes_impl(self.handle, impl))
+
     def autotune(self, key_len: int = 32, max_bytes: int = 256 << 20) -> bytes:
         """gcm_ctx_autotune: returns the 64-entry table (tile log2 per size class)."""
         buf = ctypes.create_string_buffer(64)

@@ -361,7 +361,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         ev1 = take_event(ctx);
     }
     if (prof) cudaEventRecord(ev0, s);
-    e = launch_fused(kf, nr, grid, s, mode);
+    e = launch_fused(kf, nr, grid, s, mode, ctx->aes_impl);
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
     if (prof) {
         cudaEventRecord(ev1, s);
@@ -806,6 +806,15 @@ int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2)
     if (tile_log2 != 0 && (tile_log2 < SEGF_MIN_LOG2 || tile_log2 > 16))
         return fail(GCM_ERR_INVALID_ARG, "tile_log2 must be 0 (automatic) or 9..16");
     ctx->forced_tile_log2 = tile_log2;
+    return GCM_OK;
+}
+
+int gcm_ctx_set_aes_impl(gcm_ctx *ctx, int impl)
+{
+    if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
+    if (impl != GCM_AES_TABLES && impl != GCM_AES_BITSLICED)
+        return fail(GCM_ERR_INVALID_ARG, "AES engine must be GCM_AES_TABLES (0) or GCM_AES_BITSLICED (1)");
+    ctx->aes_impl = impl;
     return GCM_OK;
 }
 

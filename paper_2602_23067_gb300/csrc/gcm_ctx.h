@@ -69,6 +69,8 @@ struct gcm_ctx {
     // (tuned_lg[floor(log2(blocks))], 0 = not tuned), else the built-in rule.
     int forced_tile_log2 = 0;
     uint8_t tuned_lg[64] = {};
+    // AES engine of the single-message fused pass (GCM_AES_TABLES / _BITSLICED).
+    int aes_impl = 0;
 };
 
 namespace gcmgpu {

@@ -178,12 +178,21 @@ __device__ __forceinline__ gf128 gf_mul(const gf128 &a, const gf128 &b)
 // them from `scratch` (16 x 8 bytes of shared memory owned by this warp) and
 // reduces the 255-bit product.  Several hundred cycles instead of the
 // several thousand of one thread doing all nine Karatsuba products.
+// Word i (0..3, not a compile-time constant) of a, by selects, so that a
+// can stay in registers.
+__device__ __forceinline__ uint32_t gf_word(const gf128 &a, int i)
+{
+    const uint32_t lo = (i & 1) ? a.w[1] : a.w[0];
+    const uint32_t hi = (i & 1) ? a.w[3] : a.w[2];
+    return (i & 2) ? hi : lo;
+}
+
 __device__ __forceinline__ gf128 gf_mul_warp(const gf128 &a, const gf128 &b, uint64_t *scratch)
 {
     const int lane = threadIdx.x & 31;
     if (lane < 16) {
         const int i = lane >> 2, j = lane & 3;
-        scratch[lane] = clmul32(brev32(a.w[i]), brev32(b.w[j]));
+        scratch[lane] = clmul32(brev32(gf_word(a, i)), brev32(gf_word(b, j)));
     }
     __syncwarp();
     uint32_t p[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};

@@ -32,6 +32,14 @@ constexpr uint32_t SM_SEGF = SM_RED + 256;  // per-warp segment factors H^((15-w
 constexpr uint32_t SM_WSCR = SM_SEGF + KF_WARPS * 16;  // per-warp scratch of gf_mul_warp (16 x 128 B)
 constexpr uint32_t SM_DSUM = SM_WSCR + KF_WARPS * 128;  // per-warp DATASUM partials (16 x 8 B)
 constexpr uint32_t KF_SMEM_BYTES = SM_DSUM + KF_WARPS * 8;
+// The bitsliced-AES form of the fused kernel (gcm_ctx_set_aes_impl = 1):
+// 256 threads (each holds 32 blocks as 128 bitsliced words, so it needs far
+// more registers than a table thread), every warp walking two of the tile's
+// 16 segments; the same shared memory plus the bitsliced round keys
+// (128 words per round, up to 15 rounds).
+constexpr int KBS_THREADS = 256;
+constexpr uint32_t SM_KBS = (KF_SMEM_BYTES + 15u) & ~15u;
+constexpr uint32_t KBS_SMEM_BYTES = SM_KBS + 128 * 15 * 4;
 
 // Per-key material, built on the device by the key-setup kernel.
 struct KeyMat {
@@ -164,7 +172,8 @@ cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream);
 cudaError_t launch_msg_only(const KsParams &p, cudaStream_t stream);
 // mode: 0 full GCM, 1 CTR keystream only, 2 GHASH only (no AES, no output),
 // 3 full GCM plus the per-tile DATASUM partials of the ciphertext side
-cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode = 0);
+// impl: 0 round tables in shared memory, 1 bitsliced AES (modes 0, 1, 3)
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode = 0, int impl = 0);
 cudaError_t launch_combine(const KcParams &p, cudaStream_t stream);
 cudaError_t launch_zero_on_fail(const KzParams &p, int grid, cudaStream_t stream);
 cudaError_t launch_batch_key_setup(const BatchMsg *msgs, const BatchKey *keys, uint32_t n,

@@ -21,6 +21,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "gcm_bitsliced.cuh"
 #include "gcm_internal.h"
 
 namespace gcmgpu {
@@ -434,7 +435,7 @@ __device__ __forceinline__ void stage_round_tables(uint8_t *smem, const DevTable
     const uint32_t *tt = tabs->ttab;
     uint4 *s128 = reinterpret_cast<uint4 *>(smem);
 #pragma unroll 4
-    for (int q = threadIdx.x; q < 8192; q += KF_THREADS) {
+    for (int q = threadIdx.x; q < 8192; q += blockDim.x) {
         const int region = q >> 12, v = (q >> 4) & 255, odd = (q >> 3) & 1;
         const uint32_t t = __ldg(&tt[(2 * region + odd) * 256 + v]);
         s128[q] = make_uint4(t, t, t, t);
@@ -445,7 +446,7 @@ __device__ __forceinline__ void stage_ghash_table(uint8_t *smem, const KeyMat *k
 {
     const uint4 *g = km->gtab;
     uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
-    for (int i = threadIdx.x; i < GTAB_ENTRIES; i += KF_THREADS) sg[i] = __ldg(&g[i]);
+    for (int i = threadIdx.x; i < GTAB_ENTRIES; i += blockDim.x) sg[i] = __ldg(&g[i]);
 }
 
 // H^((15-w) * S) for every warp w, S = 2^(tile_log2 - 4): moves a warp's
@@ -459,9 +460,77 @@ __device__ __forceinline__ void stage_segment_factors(uint8_t *smem, const KeyMa
 }
 
 // Per-CTA cache of the counter-group constants of AES round 2.
+// P0..P3 are the parts of G0..G3 that do not depend on counter byte 14
+// (bytes 12 and 13 change only every 2^16 counters), valid for grp >> 8.
 struct GroupCache {
-    uint32_t grp, G0, G1, G2, G3;
+    uint32_t grp, G0, G1, G2, G3, P0, P1, P2, P3;
 };
+
+// A segment that touches the AAD or the final partial block: lane l takes
+// blocks l, l + 32, ... of the segment, each with a whole AES computation
+// (counter = inc32^(j+1)(J0) for payload block j), and chains them into its
+// Horner accumulator (acc <- acc * H^32 xor X).  rk holds the round keys (at
+// least words 12 .. 4 NR + 3).
+template <int NR, int MODE>
+__device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgView &v, const MsgConst &c,
+                                                const uint32_t *rk, const LaneConst &L, int64_t seg_lo,
+                                                uint32_t seg_len, uint4 &acc, uint32_t &dlast, bool &have,
+                                                uint64_t &dsum)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    const KeyMat *km = v.km;
+    uint32_t rlo[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) rlo[i] = __ldg(&km->rk[i]);
+    for (uint32_t q = lane; q < seg_len; q += 32) {
+        const uint64_t s = (uint64_t)seg_lo + q;
+        uint4 x;
+        if (s < v.a_blocks) {
+            const uint64_t off = s * 16u;
+            const uint64_t rem = v.aad_len - off;
+            const uint8_t *src = v.aad + off;
+            if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
+                x = *reinterpret_cast<const uint4 *>(src);
+            else
+                x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
+        } else if (MODE == MODE_GHASH) {
+            const uint64_t j = s - v.a_blocks;
+            x = (j < v.n_full) ? __ldcs(reinterpret_cast<const uint4 *>(v.in) + j)
+                               : load_partial(v.in + j * 16u, (uint32_t)(v.len - j * 16u));
+        } else {
+            const uint64_t j = s - v.a_blocks;
+            const uint32_t ctr = c.ctr0 + 1u + (uint32_t)j;
+            uint32_t s0 = c.j0w0 ^ rlo[0], s1 = c.j0w1 ^ rlo[1], s2 = c.j0w2 ^ rlo[2];
+            uint32_t s3 = bswap32(ctr) ^ rlo[3];
+            aes_round(t01, t23, L, s0, s1, s2, s3, rlo[4], rlo[5], rlo[6], rlo[7]);
+            aes_round(t01, t23, L, s0, s1, s2, s3, rlo[8], rlo[9], rlo[10], rlo[11]);
+            uint4 ks = aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
+            if (j < v.n_full) {
+                const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(v.in) + j);
+                ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                __stcs(reinterpret_cast<uint4 *>(v.out) + j, ks);
+                x = v.dec ? din : ks;
+            } else {
+                const uint32_t nb = (uint32_t)(v.len - j * 16u);
+                const uint4 din = load_partial(v.in + j * 16u, nb);
+                ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
+                const uint4 cb = keep_bytes(ks, nb);
+                store_partial(v.out + j * 16u, cb, nb);
+                x = v.dec ? din : cb;
+            }
+        }
+        if (MODE != MODE_CTR) {
+            uint4 m = ghash_mul_table(smem, acc, L);
+            xor4(m, x);
+            acc = m;
+            dlast = q;
+            have = true;
+            if (MODE == MODE_GCM_SUM && s >= v.a_blocks) dsum += word_sum_be(x);
+        }
+    }
+}
 
 // One tile: Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C
 // are aligned to its end (the first tile is the short one; it is treated as
@@ -546,15 +615,22 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 }
                 if ((W >> 8) != gc.grp) {
                     // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
-                    gc.grp = W >> 8;
                     const uint32_t x3g = bswap32(W) ^ c.rk3;
+                    if ((W >> 16) != (gc.grp >> 8)) {
+                        // Bytes 12 or 13 changed too (every 2^16 counters).
+                        const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
+                        const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
+                        gc.P0 = LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
+                        gc.P1 = LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
+                        gc.P2 = LT0(u2, 0) ^ LT1(u3, 1) ^ __ldg(&km->rk[10]);
+                        gc.P3 = LT0(u3, 0) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
+                    }
+                    gc.grp = W >> 8;
                     const uint32_t u1 = c.K1 ^ LT2(x3g, 2);
-                    const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
-                    const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
-                    gc.G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
-                    gc.G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
-                    gc.G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
-                    gc.G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
+                    gc.G0 = LT1(u1, 1) ^ gc.P0;
+                    gc.G1 = LT0(u1, 0) ^ gc.P1;
+                    gc.G2 = LT3(u1, 3) ^ gc.P2;
+                    gc.G3 = LT2(u1, 2) ^ gc.P3;
                 }
                 // Round 1 column 0 (the only column that sees counter byte 15),
                 // then round 2 (one varying lookup per column).
@@ -578,55 +654,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
             }
         } else {
             // Segments that touch the AAD or the final partial block.
-            uint32_t rlo[12];
-#pragma unroll
-            for (int i = 0; i < 12; i++) rlo[i] = __ldg(&km->rk[i]);
-            for (uint32_t q = lane; q < seg_len; q += 32) {
-                const uint64_t s = (uint64_t)seg_lo + q;
-                uint4 x;
-                if (s < v.a_blocks) {
-                    const uint64_t off = s * 16u;
-                    const uint64_t rem = v.aad_len - off;
-                    const uint8_t *src = v.aad + off;
-                    if (rem >= 16 && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0))
-                        x = *reinterpret_cast<const uint4 *>(src);
-                    else
-                        x = load_partial(src, rem >= 16 ? 16u : (uint32_t)rem);
-                } else if (MODE == MODE_GHASH) {
-                    const uint64_t j = s - v.a_blocks;
-                    x = (j < v.n_full) ? __ldcs(reinterpret_cast<const uint4 *>(v.in) + j)
-                                       : load_partial(v.in + j * 16u, (uint32_t)(v.len - j * 16u));
-                } else {
-                    const uint64_t j = s - v.a_blocks;
-                    const uint32_t ctr = c.ctr0 + 1u + (uint32_t)j;
-                    uint32_t s0 = c.j0w0 ^ rlo[0], s1 = c.j0w1 ^ rlo[1], s2 = c.j0w2 ^ rlo[2];
-                    uint32_t s3 = bswap32(ctr) ^ rlo[3];
-                    aes_round(t01, t23, L, s0, s1, s2, s3, rlo[4], rlo[5], rlo[6], rlo[7]);
-                    aes_round(t01, t23, L, s0, s1, s2, s3, rlo[8], rlo[9], rlo[10], rlo[11]);
-                    uint4 ks = aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
-                    if (j < v.n_full) {
-                        const uint4 din = __ldcs(reinterpret_cast<const uint4 *>(v.in) + j);
-                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                        __stcs(reinterpret_cast<uint4 *>(v.out) + j, ks);
-                        x = v.dec ? din : ks;
-                    } else {
-                        const uint32_t nb = (uint32_t)(v.len - j * 16u);
-                        const uint4 din = load_partial(v.in + j * 16u, nb);
-                        ks.x ^= din.x; ks.y ^= din.y; ks.z ^= din.z; ks.w ^= din.w;
-                        const uint4 cb = keep_bytes(ks, nb);
-                        store_partial(v.out + j * 16u, cb, nb);
-                        x = v.dec ? din : cb;
-                    }
-                }
-                if (MODE != MODE_CTR) {
-                    uint4 m = ghash_mul_table(smem, acc, L);
-                    xor4(m, x);
-                    acc = m;
-                    dlast = q;
-                    have = true;
-                    if (MODE == MODE_GCM_SUM && s >= v.a_blocks) dsum += word_sum_be(x);
-                }
-            }
+            segment_general<NR, MODE>(smem, v, c, rk, L, seg_lo, seg_len, acc, dlast, have, dsum);
         }
     }
     if (MODE == MODE_CTR) return;  // no authenticator: nothing to reduce
@@ -643,13 +671,12 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     // Every lane holds the warp's sum z; the whole warp multiplies it by the
     // segment factor (warp-uniform branch).
     if (warp != KF_WARPS - 1) {
-        gf128 f;
-        if (lg == v.tile_log2) {
-            f = segf[warp];
-        } else {
-            const gf128 *g = &km->segf[lg - SEGF_MIN_LOG2][warp];
-#pragma unroll
-            for (int k = 0; k < 4; k++) f.w[k] = __ldg(&g->w[k]);
+        // The staged factor, or for a first tile laid out smaller the one of
+        // its size from the key material.
+        gf128 f = segf[warp];
+        if (lg != v.tile_log2) {
+            const uint4 g = __ldg(reinterpret_cast<const uint4 *>(&km->segf[lg - SEGF_MIN_LOG2][warp]));
+            f.w[0] = g.x; f.w[1] = g.y; f.w[2] = g.z; f.w[3] = g.w;
         }
         z = gf_mul_warp(z, f, reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
     }
@@ -714,9 +741,174 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
                                                    __ldg(&p.mm->j0[2]), __ldg(&p.mm->j0[3]));
     GroupCache gc;
     gc.grp = 0xFFFFFFFFu;
-    gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
+    gc.G0 = gc.G1 = gc.G2 = gc.G3 = gc.P0 = gc.P1 = gc.P2 = gc.P3 = 0u;
     for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
         tile_body<NR, MODE>(smem, v, c, rk, L, tile, gc);
+}
+
+// ---------------------------------------------------------------------
+// KF, bitsliced: the same tiles, segments and GHASH chains, with the CTR
+// keystream of whole-payload segments computed by bitsliced AES
+// ---------------------------------------------------------------------
+// A warp walks a whole-payload segment in windows of 1024 blocks from the
+// segment start; lane l holds blocks l, l + 32, ..., l + 992 of a window as
+// one bitsliced state (block k of the lane = bit k of every word), so the
+// lane's blocks are exactly the next 32 links of its stride-32 Horner chain.
+// Counters come from the segment's first counter (inc32 arithmetic, any
+// alignment); they are transposed into bytes 12..15 of the state.  After the
+// rounds the state is transposed back to 32 blocks of four memory words,
+// which are xored with the input, stored and hashed in chain order.
+// Segments touching the AAD or the final partial block use the table path.
+// Each of the 8 warps walks segments w and w + 8 of the tile.
+template <int NR, int MODE>
+__device__ __forceinline__ void tile_body_bs(uint8_t *smem, const MsgView &v, const MsgConst &c, const LaneConst &L,
+                                             uint64_t tile)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const KeyMat *km = v.km;
+    const uint32_t *kbs = reinterpret_cast<const uint32_t *>(smem + SM_KBS);
+    const gf128 *segf = reinterpret_cast<const gf128 *>(smem + SM_SEGF);
+    gf128 *red = reinterpret_cast<gf128 *>(smem + SM_RED);
+    const int64_t tend = (int64_t)v.M - (int64_t)((v.K - 1 - tile) << v.tile_log2);
+    uint32_t lg = v.tile_log2;
+    if (tile == 0)
+        while (lg > (uint32_t)SEGF_MIN_LOG2 && ((int64_t)1 << (lg - 1)) >= tend) lg--;
+    const int64_t seg_blocks = (int64_t)1 << (lg - KF_LOG2_WARPS);
+    const int64_t tv_lo = tend - ((int64_t)1 << lg);
+    gf128 zw = gf_zero();
+    uint64_t dsum = 0;
+
+    for (int sw = warp; sw < KF_WARPS; sw += nwarps) {
+        const int64_t seg_hi = tv_lo + (int64_t)(sw + 1) * seg_blocks;
+        int64_t seg_lo = tv_lo + (int64_t)sw * seg_blocks;
+        if (seg_lo < 0) seg_lo = 0;
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        uint32_t dlast = 0, seg_len = 0;
+        bool have = false;
+        if (seg_hi > seg_lo) {
+            seg_len = (uint32_t)(seg_hi - seg_lo);
+            if ((uint64_t)seg_lo >= v.a_blocks && (uint64_t)seg_hi <= v.a_blocks + v.n_full) {
+                const uint64_t j_lo = (uint64_t)seg_lo - v.a_blocks;
+                const uint32_t c_lo = c.ctr0 + 1u + (uint32_t)j_lo;
+                const uint4 *in = reinterpret_cast<const uint4 *>(v.in) + j_lo;
+                uint4 *out = reinterpret_cast<uint4 *>(v.out) + j_lo;
+                for (uint32_t base = 0; base < seg_len; base += 1024u) {
+                    uint32_t s[128];
+                    {
+                        uint32_t ctr[32];
+#pragma unroll
+                        for (int k = 0; k < 32; k++) ctr[k] = c_lo + base + lane + 32u * (uint32_t)k;
+                        load_counters_bs(s, c.j0w0, c.j0w1, c.j0w2, ctr, kbs);
+                    }
+                    aes_rounds_bs<NR>(s, kbs);
+                    unload_blocks_bs(s);
+#pragma unroll
+                    for (int k = 0; k < 32; k++) {
+                        const uint32_t d = base + lane + 32u * (uint32_t)k;
+                        if (d < seg_len) {
+                            const uint4 din = __ldcs(in + d);
+                            const uint4 ks = make_uint4(s[k] ^ din.x, s[32 + k] ^ din.y, s[64 + k] ^ din.z,
+                                                        s[96 + k] ^ din.w);
+                            __stcs(out + d, ks);
+                            if (MODE == MODE_GCM || MODE == MODE_GCM_SUM) {
+                                const uint4 x = v.dec ? din : ks;
+                                uint4 m = ghash_mul_table(smem, acc, L);
+                                xor4(m, x);
+                                acc = m;
+                                dlast = d;
+                                have = true;
+                                if (MODE == MODE_GCM_SUM) dsum += word_sum_be(x);
+                            }
+                        }
+                    }
+                }
+            } else {
+                segment_general<NR, MODE>(smem, v, c, km->rk, L, seg_lo, seg_len, acc, dlast, have, dsum);
+            }
+        }
+        if (MODE != MODE_CTR) {
+            // Close the lane chains, reduce the warp, move the segment's
+            // partial to the tile end and add it to the warp's sum.
+            gf128 z = gf_zero();
+            if (have) z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), km->hpow[seg_len - dlast - 1]);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
+            if (sw != KF_WARPS - 1) {
+                gf128 f = segf[sw];
+                if (lg != v.tile_log2) {
+                    const uint4 g = __ldg(reinterpret_cast<const uint4 *>(&km->segf[lg - SEGF_MIN_LOG2][sw]));
+                    f.w[0] = g.x; f.w[1] = g.y; f.w[2] = g.z; f.w[3] = g.w;
+                }
+                z = gf_mul_warp(z, f, reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp);
+            }
+            zw = gf_xor(zw, z);
+        }
+    }
+    if (MODE == MODE_CTR) return;  // no authenticator: nothing to reduce
+    if (lane == 0) red[warp] = zw;
+    uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
+    if (MODE == MODE_GCM_SUM) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, off);
+        if (lane == 0) dred[warp] = dsum;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        gf128 z = (lane < (uint32_t)nwarps) ? red[lane] : gf_zero();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) z.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, z.w[k], off);
+        if (lane == 0) v.partials[tile] = z;
+        if (MODE == MODE_GCM_SUM) {
+            dsum = (lane < (uint32_t)nwarps) ? dred[lane] : 0ull;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) dsum += __shfl_xor_sync(0xFFFFFFFFu, dsum, off);
+            if (lane == 0) v.dsums[tile] = ones_fold(dsum);
+        }
+    }
+    __syncthreads();
+}
+
+template <int NR, int MODE>
+__global__ void __launch_bounds__(KBS_THREADS, 1) fused_bs_kernel(const __grid_constant__ KfParams p)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    stage_round_tables(smem, p.tabs);
+    if (MODE != MODE_CTR) stage_ghash_table(smem, p.km);
+    if (threadIdx.x < KF_WARPS)
+        reinterpret_cast<gf128 *>(smem + SM_SEGF)[threadIdx.x] =
+            p.km->segf[p.tile_log2 - SEGF_MIN_LOG2][threadIdx.x];
+    uint32_t *kbs = reinterpret_cast<uint32_t *>(smem + SM_KBS);
+    for (int q = threadIdx.x; q < 128 * (NR + 1); q += blockDim.x) kbs[q] = round_key_word_bs(p.km->rk, q);
+    const LaneConst L = make_lane_const((int)(threadIdx.x & 31));
+    MsgView v;
+    v.in = p.in;
+    v.out = p.out;
+    v.aad = p.aad;
+    v.len = p.len;
+    v.aad_len = p.aad_len;
+    v.a_blocks = p.a_blocks;
+    v.n_full = p.n_full;
+    v.M = p.M;
+    v.K = p.K;
+    v.tile_log2 = p.tile_log2;
+    v.dec = p.decrypt != 0;
+    v.km = p.km;
+    v.mm = p.mm;
+    v.partials = p.partials;
+    v.dsums = p.dsums;
+    __syncthreads();
+    const MsgConst c = p.j0_given ? make_msg_const(t01, t23, L, p.km, p.j0[0], p.j0[1], p.j0[2], p.j0[3])
+                                  : make_msg_const(t01, t23, L, p.km, __ldg(&p.mm->j0[0]), __ldg(&p.mm->j0[1]),
+                                                   __ldg(&p.mm->j0[2]), __ldg(&p.mm->j0[3]));
+    for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
+        tile_body_bs<NR, MODE>(smem, v, c, L, tile);
 }
 
 // ---------------------------------------------------------------------
@@ -1139,6 +1331,19 @@ cudaError_t configure_kernels()
     SET_SMEM((fused_kernel<12, MODE_GCM_SUM>));
     SET_SMEM((fused_kernel<14, MODE_GCM_SUM>));
 #undef SET_SMEM
+#define SET_SMEM_BS(K)                                                                          \
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, KBS_SMEM_BYTES); \
+    if (e != cudaSuccess) return e;
+    SET_SMEM_BS((fused_bs_kernel<10, MODE_GCM>));
+    SET_SMEM_BS((fused_bs_kernel<12, MODE_GCM>));
+    SET_SMEM_BS((fused_bs_kernel<14, MODE_GCM>));
+    SET_SMEM_BS((fused_bs_kernel<10, MODE_CTR>));
+    SET_SMEM_BS((fused_bs_kernel<12, MODE_CTR>));
+    SET_SMEM_BS((fused_bs_kernel<14, MODE_CTR>));
+    SET_SMEM_BS((fused_bs_kernel<10, MODE_GCM_SUM>));
+    SET_SMEM_BS((fused_bs_kernel<12, MODE_GCM_SUM>));
+    SET_SMEM_BS((fused_bs_kernel<14, MODE_GCM_SUM>));
+#undef SET_SMEM_BS
     return cudaSuccess;
 }
 
@@ -1160,9 +1365,23 @@ cudaError_t launch_key_setup(const KsParams &p, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode)
+cudaError_t launch_fused(const KfParams &p, int nr, int grid, cudaStream_t stream, int mode, int impl)
 {
     if (p.tile_end <= p.tile_begin) return cudaSuccess;
+    if (impl == 1 && mode != MODE_GHASH) {
+#define KBS_LAUNCH(NRV)                                                                                             \
+    if (mode == MODE_CTR) fused_bs_kernel<NRV, MODE_CTR><<<grid, KBS_THREADS, KBS_SMEM_BYTES, stream>>>(p);         \
+    else if (mode == MODE_GCM_SUM) fused_bs_kernel<NRV, MODE_GCM_SUM><<<grid, KBS_THREADS, KBS_SMEM_BYTES, stream>>>(p); \
+    else fused_bs_kernel<NRV, MODE_GCM><<<grid, KBS_THREADS, KBS_SMEM_BYTES, stream>>>(p);
+        switch (nr) {
+        case 10: KBS_LAUNCH(10); break;
+        case 12: KBS_LAUNCH(12); break;
+        case 14: KBS_LAUNCH(14); break;
+        default: return cudaErrorInvalidValue;
+        }
+#undef KBS_LAUNCH
+        return cudaGetLastError();
+    }
     if (mode == MODE_GHASH) {
         fused_kernel<14, MODE_GHASH><<<grid, KF_THREADS, KF_SMEM_BYTES, stream>>>(p);
         return cudaGetLastError();
