@@ -8,9 +8,11 @@
 // all messages (one CTA each), the persistent batched kernel over
 // (message, tile) items, and -- for decryption -- the zero-fill of messages
 // whose tag failed.  The verdicts come back with one small copy.
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <numeric>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -64,15 +66,25 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
         }
     } restore{prev};
 
-    // Sizes and the layout of one scratch allocation.
+    // Work items go out shortest message first: slot j of the launch holds
+    // message order[j], so short messages finish early and the median
+    // completion time drops (results do not depend on the order).  Verdicts
+    // and completion times are mapped back to the caller's order.
+    std::vector<uint64_t> Mlen(n);
+    for (size_t i = 0; i < n; i++) Mlen[i] = (msgs[i].aad_len + 15) / 16 + (msgs[i].len + 15) / 16;
+    std::vector<size_t> order(n);
+    std::iota(order.begin(), order.end(), (size_t)0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return Mlen[a] < Mlen[b]; });
+
+    // Sizes and the layout of one scratch allocation (indexed by slot).
     std::vector<uint64_t> K(n), base(n), o_km(n), o_part(n), o_tree(n), o_iv(n);
     uint64_t items = 0;
-    for (size_t i = 0; i < n; i++) {
-        const uint64_t M = (msgs[i].aad_len + 15) / 16 + (msgs[i].len + 15) / 16;
+    for (size_t j = 0; j < n; j++) {
+        const uint64_t M = Mlen[order[j]];
         uint64_t k = (M + (1ull << BATCH_TILE_LOG2) - 1) >> BATCH_TILE_LOG2;
         if (k == 0) k = 1;  // an empty message still has one (empty) tile, so its tag gets computed
-        K[i] = k;
-        base[i] = items;
+        K[j] = k;
+        base[j] = items;
         items += k;
     }
     size_t off = 0;
@@ -82,9 +94,9 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     off = al(off + n * sizeof(BatchKey));
     const size_t o_ivs = off;
     size_t iv_total = 0;
-    for (size_t i = 0; i < n; i++) {
-        o_iv[i] = iv_total;
-        iv_total += msgs[i].iv_len;
+    for (size_t j = 0; j < n; j++) {
+        o_iv[j] = iv_total;
+        iv_total += msgs[order[j]].iv_len;
     }
     off = al(off + iv_total);
     const size_t host_bytes = off;  // everything above is filled on the host
@@ -131,8 +143,8 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     BatchMsg *hm = reinterpret_cast<BatchMsg *>(stage + o_msgs);
     BatchKey *hk = reinterpret_cast<BatchKey *>(stage + o_keys);
     uint8_t *hiv = stage + o_ivs;
-    for (size_t i = 0; i < n; i++) {
-        const gcm_msg &m = msgs[i];
+    for (size_t i = 0; i < n; i++) {  // i = slot
+        const gcm_msg &m = msgs[order[i]];
         BatchMsg &b = hm[i];
         memset(&b, 0, sizeof(b));
         b.in = m.in;
@@ -186,7 +198,7 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     if (prof) {
         cudaEventRecord(p1, s);
         uint64_t bytes = 0;
-        for (size_t i = 0; i < n; i++) bytes += 2 * msgs[i].len + msgs[i].aad_len;
+        for (size_t i = 0; i < n; i++) bytes += 2 * msgs[i].len + msgs[i].aad_len;  // order-free
         ctx_record_fused(ctx, p0, p1, bytes);
     }
     ctx->launches += 1;
@@ -204,9 +216,9 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ctx_cuda_fail(e, "batched launch");
     if (status)
-        for (size_t i = 0; i < n; i++) status[i] = hstat[i] ? GCM_ERR_AUTH : 0;
+        for (size_t j = 0; j < n; j++) status[order[j]] = hstat[j] ? GCM_ERR_AUTH : 0;
     if (done_ns)
-        for (size_t i = 0; i < n; i++) done_ns[i] = htimes[1 + i] - htimes[0];
+        for (size_t j = 0; j < n; j++) done_ns[order[j]] = htimes[1 + j] - htimes[0];
     return GCM_OK;
 }
 
