@@ -12,6 +12,9 @@
 //                 Sec. 5.2: block j always uses inc32^(j+1)(J0)) fused with
 //                 the GHASH map: every CTA reduces tiles of the GHASH input
 //                 sequence A||C to 16-byte partials (Sec. 5.2.3, map phase).
+//   KF' fused_bs  the same pass with the CTR keystream from bitsliced AES
+//                 (32 blocks per thread; the paper's own AES core is
+//                 bit-sliced, Sec. 5.2), selected per context.
 //   KC  combine   log-depth tree over the tile partials with multipliers
 //                 H^(2^k) (Sec. 3.3.1, Fig. 2b; Sec. 5.2.3 reduce phase),
 //                 the length block and T = E_K(J0) xor GHASH; for decryption
@@ -327,7 +330,8 @@ __device__ __forceinline__ uint4 aes_rounds_from3(const uint8_t *t01, const uint
                                                   const uint32_t *rk)
 {
 #pragma unroll
-    for (int r = 3; r < NR; r++) aes_round(t01, t23, L, s0, s1, s2, s3, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
+    for (int r = 3; r < NR; r++)
+        aes_round(t01, t23, L, s0, s1, s2, s3, rk[4 * r], rk[4 * r + 1], rk[4 * r + 2], rk[4 * r + 3]);
     uint4 o;
     o.x = aes_last_col(t01, t23, L, s0, s1, s2, s3, rk[4 * NR + 0]);
     o.y = aes_last_col(t01, t23, L, s1, s2, s3, s0, rk[4 * NR + 1]);
@@ -535,11 +539,13 @@ __device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgVi
 // One tile: Tiles of 2^tile_log2 blocks of the GHASH input sequence A||C
 // are aligned to its end (the first tile is the short one; it is treated as
 // the smallest tile of 2^lg >= its length blocks, left-padded with zero
-// blocks).  Warp w owns segment w of the tile (S = 2^lg/16 blocks).  On whole-payload segments the warp walks windows
-// of 32 counters aligned to multiples of 32, so a window never crosses a
-// 256-counter group: rounds 1 and 2 of AES then need only the lookups that
-// depend on the counter's low byte (counter-mode caching; the rest are
-// per-group constants computed once per 256 counters).  Lane l chains the
+// blocks).  Warp w owns segment w of the tile (S = 2^lg/16 blocks).  On
+// whole-payload segments the warp walks windows of 32 counters aligned to
+// multiples of 32, so a window never crosses a 256-counter group: rounds 1
+// and 2 of AES then need only the lookups that depend on the counter's low
+// byte (counter-mode caching; the rest are per-group constants computed
+// once per 256 counters, and only the counter-byte-14 part of them when
+// bytes 12 and 13 stay the same).  Lane l chains the
 // l-th block of every window through acc <- acc*H^32 xor X and closes the
 // chain with H^e, e = distance of its last block from the segment end; the
 // warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
@@ -1054,7 +1060,8 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
             // New message: its key's GHASH table and segment factors.
             stage_ghash_table(smem, bm.km);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            if (lane == 0) reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[BATCH_TILE_LOG2 - SEGF_MIN_LOG2][warp];
+            if (lane == 0)
+                reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[BATCH_TILE_LOG2 - SEGF_MIN_LOG2][warp];
             cur = mi;
             gc.grp = 0xFFFFFFFFu;
             __syncthreads();
