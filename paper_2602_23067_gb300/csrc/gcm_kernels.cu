@@ -464,10 +464,8 @@ __device__ __forceinline__ void stage_segment_factors(uint8_t *smem, const KeyMa
 }
 
 // Per-CTA cache of the counter-group constants of AES round 2.
-// P0..P3 are the parts of G0..G3 that do not depend on counter byte 14
-// (bytes 12 and 13 change only every 2^16 counters), valid for grp >> 8.
 struct GroupCache {
-    uint32_t grp, G0, G1, G2, G3, P0, P1, P2, P3;
+    uint32_t grp, G0, G1, G2, G3;
 };
 
 // A segment that touches the AAD or the final partial block: lane l takes
@@ -544,8 +542,7 @@ __device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgVi
 // multiples of 32, so a window never crosses a 256-counter group: rounds 1
 // and 2 of AES then need only the lookups that depend on the counter's low
 // byte (counter-mode caching; the rest are per-group constants computed
-// once per 256 counters, and only the counter-byte-14 part of them when
-// bytes 12 and 13 stay the same).  Lane l chains the
+// once per 256 counters).  Lane l chains the
 // l-th block of every window through acc <- acc*H^32 xor X and closes the
 // chain with H^e, e = distance of its last block from the segment end; the
 // warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
@@ -621,22 +618,15 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 }
                 if ((W >> 8) != gc.grp) {
                     // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
-                    const uint32_t x3g = bswap32(W) ^ c.rk3;
-                    if ((W >> 16) != (gc.grp >> 8)) {
-                        // Bytes 12 or 13 changed too (every 2^16 counters).
-                        const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
-                        const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
-                        gc.P0 = LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
-                        gc.P1 = LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
-                        gc.P2 = LT0(u2, 0) ^ LT1(u3, 1) ^ __ldg(&km->rk[10]);
-                        gc.P3 = LT0(u3, 0) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
-                    }
                     gc.grp = W >> 8;
+                    const uint32_t x3g = bswap32(W) ^ c.rk3;
                     const uint32_t u1 = c.K1 ^ LT2(x3g, 2);
-                    gc.G0 = LT1(u1, 1) ^ gc.P0;
-                    gc.G1 = LT0(u1, 0) ^ gc.P1;
-                    gc.G2 = LT3(u1, 3) ^ gc.P2;
-                    gc.G3 = LT2(u1, 2) ^ gc.P3;
+                    const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
+                    const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
+                    gc.G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
+                    gc.G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
+                    gc.G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
+                    gc.G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
                 }
                 // Round 1 column 0 (the only column that sees counter byte 15),
                 // then round 2 (one varying lookup per column).
@@ -747,7 +737,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
                                                    __ldg(&p.mm->j0[2]), __ldg(&p.mm->j0[3]));
     GroupCache gc;
     gc.grp = 0xFFFFFFFFu;
-    gc.G0 = gc.G1 = gc.G2 = gc.G3 = gc.P0 = gc.P1 = gc.P2 = gc.P3 = 0u;
+    gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
     for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
         tile_body<NR, MODE>(smem, v, c, rk, L, tile, gc);
 }
