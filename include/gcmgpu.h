@@ -466,8 +466,14 @@ int gfc_fits_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
  *   HDU 1: a one-row binary table (TFORM1 = '<N>B', TTYPE1 = 'ENCDATA')
  *     holding the N pixel bytes encrypted with the data key under NONCE_D
  *     with AAD_D = NONCE_D || Serialize(ORIG_BITPIX) || Serialize(ORIG_NAXIS)
- *     || Serialize(ORIG_NAXIS1) || ... (Sec. 3.2.3), and its DATASUM (from the
- *     same pass; omitted on the staged host path).
+ *     || Serialize(ORIG_NAXIS1) || ... (Sec. 3.2.3).
+ *   Both HDUs end with the FITS-standard DATASUM and CHECKSUM keywords
+ *   (Sec. 3.2.2; FITS checksum convention): DATASUM is the 32-bit ones'
+ *   complement sum of the data unit ('0' for HDU 0, which has none; for
+ *   HDU 1 computed in the encryption pass) and CHECKSUM the 16-character
+ *   encoding of the complement of the HDU's sum, so that each HDU sums to
+ *   -0.  On the staged host path, which computes no data sum, HDU 1 carries
+ *   neither.
  * key_h/key_d: 16/24/32-byte keys (host).  nonce_h/nonce_d: 12 host bytes,
  * or NULL to draw them from the operating system's entropy source.  fits is
  * in the memory given by mem; out->data_buffer receives the container.

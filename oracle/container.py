@@ -18,8 +18,13 @@ readings where the paper is silent):
   TTYPE1 = 'ENCDATA'): the original pixel bytes (the data unit without its
   record padding, N = |BITPIX|/8 * prod NAXISn) encrypted with the data key
   under NONCE_D with AAD_D = NONCE_D || Serialize(ORIG_BITPIX) ||
-  Serialize(ORIG_NAXIS) || Serialize(ORIG_NAXIS1) || ... (Sec. 3.2.3), and
-  DATASUM of that data unit (FITS checksum convention).
+  Serialize(ORIG_NAXIS) || Serialize(ORIG_NAXIS1) || ... (Sec. 3.2.3).
+* Both HDUs end with DATASUM and CHECKSUM cards (Sec. 3.2.2: the container
+  carries the FITS-standard CHECKSUM/DATASUM keywords in both HDUs): DATASUM
+  is the 32-bit ones' complement sum of the data unit ('0' for the primary,
+  which has none) and CHECKSUM the 16-character encoding, defined by the FITS
+  checksum convention the paper cites, of the complement of the HDU's sum,
+  so that the whole HDU then sums to -0 (0xFFFFFFFF).
 
 Decryption (the paper's gfc_decrypt_frame): the header is the authenticated
 ENCHDR when the header key is given and its tag verifies, else a minimal
@@ -79,6 +84,55 @@ def header_block(cards: Sequence[bytes]) -> bytes:
     return h + b" " * ((-len(h)) % RECORD)
 
 
+def ones_add(a: int, b: int) -> int:
+    """Ones' complement sum of two 32-bit ones' complement sums."""
+    s = a + b
+    while s >> 32:
+        s = (s & 0xFFFFFFFF) + (s >> 32)
+    return s
+
+
+_PUNCT = set(range(0x3A, 0x41)) | set(range(0x5B, 0x61))
+
+
+def checksum_chars(value: int) -> str:
+    """The 16 ASCII characters that stand for a 32-bit value in a CHECKSUM
+    card.  Byte i of the value (i = 0 most significant) becomes four
+    characters whose codes add up to the byte plus 4 * 0x30: all equal to
+    0x30 + byte // 4, the first raised by byte % 4.  Characters that would be
+    punctuation (0x3A..0x40, 0x5B..0x60) are avoided by moving one unit from
+    the second to the first character of a pair ((0,1) and (2,3)), which
+    keeps the pair's sum, until neither is punctuation.  The four characters
+    of byte i go to positions i, i+4, i+8, i+12, so in 4-byte words each
+    byte lane adds up to the value's byte plus 4 * 0x30; the string is then
+    rotated right by one, because a card value starts at column 12, one byte
+    before a word boundary of the header."""
+    out = [0] * 16
+    for i in range(4):
+        byte = (value >> (24 - 8 * i)) & 0xFF
+        c = [0x30 + byte // 4] * 4
+        c[0] += byte % 4
+        for j in (0, 2):
+            while c[j] in _PUNCT or c[j + 1] in _PUNCT:
+                c[j] += 1
+                c[j + 1] -= 1
+        for j in range(4):
+            out[4 * j + i] = c[j]
+    rotated = out[15:] + out[:15]
+    return bytes(rotated).decode("ascii")
+
+
+def header_with_checksum(cards: Sequence[bytes], data_sum: int, data_sum_text: str) -> bytes:
+    """The header block of cards + DATASUM + CHECKSUM, the CHECKSUM value
+    chosen so that header and data together sum to -0."""
+    zero = "0" * 16
+    h = header_block(list(cards) + [card_str("DATASUM", data_sum_text), card_str("CHECKSUM", zero)])
+    total = ones_add(datasum(h), data_sum)
+    at = h.index(("CHECKSUM= '%s'" % zero).encode("ascii")) + 11
+    enc = checksum_chars(~total & 0xFFFFFFFF).encode("ascii")
+    return h[:at] + enc + h[at + 16:]
+
+
 def parse_header(buf: bytes, off: int = 0) -> Tuple[Dict[str, str], int]:
     """Keyword -> raw value text (strings without quotes; long strings joined
     over CONTINUE cards), and the offset just past the header's last record."""
@@ -133,11 +187,12 @@ def container_encrypt(key_h: bytes, key_d: bytes, nonce_h: bytes, nonce_d: bytes
              card_int("ORIG_BPX", bitpix), card_int("ORIG_NAX", len(naxes))]
     cards += [card_int("ORIG_NA%d" % (i + 1), n) for i, n in enumerate(naxes)]
     cards += cards_long_str("ENCHDR", enchdr.hex())
-    primary = header_block(cards)
-    ext = header_block([card_str("XTENSION", "BINTABLE"), card_int("BITPIX", 8), card_int("NAXIS", 2),
-                        card_int("NAXIS1", len(blob)), card_int("NAXIS2", 1), card_int("PCOUNT", 0),
-                        card_int("GCOUNT", 1), card_int("TFIELDS", 1), card_str("TTYPE1", "ENCDATA"),
-                        card_str("TFORM1", "%dB" % len(blob)), card_str("DATASUM", str(datasum(blob)))])
+    primary = header_with_checksum(cards, 0, "0")
+    dsum = datasum(blob)
+    ext = header_with_checksum([card_str("XTENSION", "BINTABLE"), card_int("BITPIX", 8), card_int("NAXIS", 2),
+                                card_int("NAXIS1", len(blob)), card_int("NAXIS2", 1), card_int("PCOUNT", 0),
+                                card_int("GCOUNT", 1), card_int("TFIELDS", 1), card_str("TTYPE1", "ENCDATA"),
+                                card_str("TFORM1", "%dB" % len(blob))], dsum, str(dsum))
     return primary + ext + blob + bytes((-len(blob)) % RECORD)
 
 

@@ -423,6 +423,69 @@ std::string header_records(const std::vector<std::string> &cards)
 
 size_t header_records_size(size_t n_cards) { return ((n_cards + 1) * CARD + REC - 1) / REC * REC; }
 
+// FITS checksum convention (the CHECKSUM / DATASUM keywords the container
+// carries in both HDUs, Sec. 3.2.2): 32-bit ones' complement arithmetic on
+// big-endian words.
+uint32_t ones_add32(uint32_t a, uint32_t b)
+{
+    uint64_t t = (uint64_t)a + b;
+    while (t >> 32) t = (t & 0xFFFFFFFFull) + (t >> 32);
+    return (uint32_t)t;
+}
+
+uint32_t ones_sum_words(const std::string &bytes)  // length a multiple of 4
+{
+    uint64_t t = 0;
+    for (size_t i = 0; i + 4 <= bytes.size(); i += 4) {
+        const uint8_t *q = reinterpret_cast<const uint8_t *>(bytes.data()) + i;
+        t += ((uint32_t)q[0] << 24) | ((uint32_t)q[1] << 16) | ((uint32_t)q[2] << 8) | (uint32_t)q[3];
+    }
+    while (t >> 32) t = (t & 0xFFFFFFFFull) + (t >> 32);
+    return (uint32_t)t;
+}
+
+// The CHECKSUM value for a 32-bit v (the complement of the HDU's sum): every
+// byte of v, most significant first, gives four characters 0x30 + byte / 4
+// with the first one raised by byte % 4, so their codes add up to the byte
+// plus 4 * 0x30; characters in the punctuation ranges 0x3A..0x40 and
+// 0x5B..0x60 are avoided by shifting one unit inside the pairs (0,1) and
+// (2,3).  Byte i's characters go to positions i, i + 4, i + 8, i + 12, and
+// the string is rotated right by one place: the value starts at column 12
+// of its card, one byte before a 4-byte boundary of the header.
+std::string checksum_value(uint32_t v)
+{
+    auto punct = [](int c) { return (c >= 0x3A && c <= 0x40) || (c >= 0x5B && c <= 0x60); };
+    char plain[16];
+    for (int i = 0; i < 4; i++) {
+        const int byte = (int)((v >> (24 - 8 * i)) & 0xFFu);
+        int c[4] = {0x30 + byte / 4 + byte % 4, 0x30 + byte / 4, 0x30 + byte / 4, 0x30 + byte / 4};
+        for (int j = 0; j < 4; j += 2)
+            while (punct(c[j]) || punct(c[j + 1])) {
+                c[j]++;
+                c[j + 1]--;
+            }
+        for (int j = 0; j < 4; j++) plain[4 * j + i] = (char)c[j];
+    }
+    std::string out(16, '0');
+    for (int k = 0; k < 16; k++) out[k] = plain[(k + 15) % 16];
+    return out;
+}
+
+// Header records of `cards` followed by DATASUM (data_sum_text) and a
+// CHECKSUM whose value makes the header together with a data unit of sum
+// data_sum add up to -0 (0xFFFFFFFF).
+std::string header_records_checksummed(std::vector<std::string> cards, uint32_t data_sum,
+                                       const std::string &data_sum_text)
+{
+    cards.push_back(kcard_str("DATASUM", data_sum_text));
+    const size_t at = cards.size() * CARD + 11;  // the CHECKSUM value's first byte
+    cards.push_back(kcard_str("CHECKSUM", std::string(16, '0')));
+    std::string h = header_records(cards);
+    const uint32_t total = ones_add32(ones_sum_words(h), data_sum);
+    h.replace(at, 16, checksum_value(~total));
+    return h;
+}
+
 constexpr size_t HEX_PER_CARD = 64;
 
 // Keyword -> value text (strings unquoted and right-trimmed, long strings
@@ -566,9 +629,9 @@ int container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, cons
     // Layout of the container.
     const std::string hx = hexs(reinterpret_cast<const uint8_t *>(enchdr.data()), enchdr.size());
     const size_t n_hex_cards = (hx.size() + HEX_PER_CARD - 1) / HEX_PER_CARD;
-    const size_t prim_cards = 10 + (size_t)L.naxis + (n_hex_cards ? n_hex_cards : 1);
+    const size_t prim_cards = 12 + (size_t)L.naxis + (n_hex_cards ? n_hex_cards : 1);  // + DATASUM, CHECKSUM
     const size_t prim_bytes = header_records_size(prim_cards);
-    const size_t ext_bytes = header_records_size(11);
+    const size_t ext_bytes = header_records_size(12);
     const size_t N = L.data_bytes;
     const size_t blob_off = prim_bytes + ext_bytes;
     const size_t total = blob_off + (N + REC - 1) / REC * REC;
@@ -632,13 +695,14 @@ int container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, cons
         pc.push_back(pad80(i == 0 ? std::string("ENCHDR  = '") + part + amp + "'"
                                   : std::string("CONTINUE  '") + part + amp + "'"));
     }
-    const std::string prim = header_records(pc);
+    const std::string prim = header_records_checksummed(pc, 0, "0");  // no data unit
     std::vector<std::string> xc = {kcard_str("XTENSION", "BINTABLE"), kcard_int("BITPIX", 8), kcard_int("NAXIS", 2),
                                    kcard_int("NAXIS1", (int64_t)N), kcard_int("NAXIS2", 1), kcard_int("PCOUNT", 0),
                                    kcard_int("GCOUNT", 1), kcard_int("TFIELDS", 1), kcard_str("TTYPE1", "ENCDATA"),
                                    kcard_str("TFORM1", std::to_string(N) + "B")};
-    if (dsum_done) xc.push_back(kcard_str("DATASUM", std::to_string(dsum)));  // omitted when not computed
-    const std::string ext = header_records(xc);
+    // DATASUM and CHECKSUM need the data unit's sum, which the staged
+    // host-memory path does not compute: there both cards are left out.
+    const std::string ext = dsum_done ? header_records_checksummed(xc, dsum, std::to_string(dsum)) : header_records(xc);
     e = put_bytes(buf, prim.data(), prim.size(), mem, s);
     if (e == cudaSuccess) e = put_bytes(buf + prim_bytes, ext.data(), ext.size(), mem, s);
     if (e == cudaSuccess && mem == GCM_MEM_DEVICE) e = cudaStreamSynchronize(s);

@@ -97,3 +97,52 @@ def test_other_shapes():
         f = _file(r.randrange(1000), n1, n2, bitpix)
         out, w = C.decrypt_frame(C.container_encrypt(KH, KD, NH, ND, f), KH, KD)
         assert w == 0 and out == f
+
+
+def _hdus(c):
+    """(header bytes, data bytes) of both HDUs of a container."""
+    _, off = C.parse_header(c, 0)
+    x, doff = C.parse_header(c, off)
+    n = int(x["NAXIS1"])
+    return [(c[:off], b""), (c[off:doff], c[doff: doff + n + (-n) % 2880])]
+
+
+@pytest.mark.parametrize("shape", [(256, 256, -32), (100, 37, 16), (1, 1, 16), (640, 3, -32)])
+def test_checksum_closes_every_hdu(shape):
+    # The defining property of CHECKSUM (FITS checksum convention, cited in
+    # Sec. 3.2.2): with the card in place the HDU sums to -0, and DATASUM is
+    # the data unit's own sum ('0' for the data-less primary HDU).
+    f = _file(7, shape[0], shape[1], shape[2])
+    c = C.container_encrypt(KH, KD, NH, ND, f)
+    for hdr, data in _hdus(c):
+        keys, _ = C.parse_header(hdr, 0)
+        assert int(keys["DATASUM"]) == (oracle.datasum(data) if data else 0)
+        assert oracle.datasum(hdr + data) == 0xFFFFFFFF
+        v = keys["CHECKSUM"]
+        assert len(v) == 16 and v.isalnum() and v.isascii()
+
+
+def test_checksum_detects_a_flipped_bit():
+    f = _file(8)
+    c = bytearray(C.container_encrypt(KH, KD, NH, ND, f))
+    r = random.Random(81)
+    (h0, _), (h1, d1) = _hdus(bytes(c))
+    for pos in [r.randrange(len(h0)), len(h0) + r.randrange(len(h1)), len(h0) + len(h1) + r.randrange(len(d1))]:
+        t = bytearray(c)
+        t[pos] ^= 1 << r.randrange(8)
+        sums = [oracle.datasum(h + d) for h, d in _hdus(bytes(t))]
+        assert sums.count(0xFFFFFFFF) == 1  # the damaged HDU no longer sums to -0, the other still does
+
+
+def test_checksum_chars_sum_per_byte_lane():
+    # Realigned to words (undo the rotation), the 16 characters add up, byte
+    # lane by byte lane, to the encoded value plus 4 * 0x30 in every lane.
+    r = random.Random(82)
+    values = [0, 1, 0xFFFFFFFF, 0x7FFFFFFF, 0x80000000, 0x3A3A3A3A, 0xE8E8E8E8] + \
+        [r.getrandbits(32) for _ in range(3000)]
+    for v in values:
+        s = C.checksum_chars(v)
+        assert s.isalnum() and len(s) == 16
+        aligned = (s[1:] + s[:1]).encode("ascii")
+        lanes = [sum(aligned[4 * j + i] for j in range(4)) for i in range(4)]
+        assert lanes == [((v >> (24 - 8 * i)) & 0xFF) + 4 * 0x30 for i in range(4)], hex(v)
