@@ -678,6 +678,7 @@ int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers)
 
 int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t *status, int mem, void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_batch");
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
     if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
     if (mem == GCM_MEM_HOST) {
@@ -708,6 +709,7 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t 
 int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t *status, uint64_t *done_ns,
                     void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_batch_timed");
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");
     if (n && !msgs) return fail(GCM_ERR_INVALID_ARG, "msgs is NULL");
     return batch_device(ctx, msgs, n, decrypt != 0, status, done_ns, static_cast<cudaStream_t>(stream));
@@ -926,6 +928,7 @@ int gcm_sync(gcm_ctx *ctx, void *stream)
 int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *iv, size_t iv_len,
                 const uint8_t *in, size_t len, uint8_t *out, void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_ctr_xor");
     static const uint8_t no_tag[1] = {0};
     int rc = check_common(ctx, key, key_len, iv, iv_len, nullptr, 0, in, len, out, no_tag, GCM_MEM_DEVICE);
     if (rc) return rc;
@@ -942,6 +945,7 @@ int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t 
 int gcm_ghash(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t *aad, size_t aad_len,
               const uint8_t *data, size_t len, uint8_t *out16, void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_ghash");
     static const uint8_t iv96[12] = {0};  // H does not depend on the IV; J0 is unused
     int rc = check_common(ctx, key, key_len, iv96, sizeof(iv96), aad, aad_len, data, len, data, out16,
                           GCM_MEM_DEVICE);
@@ -960,6 +964,7 @@ int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t 
                 const uint8_t *aad, size_t aad_len, const uint8_t *pt, size_t len, uint8_t *ct, uint8_t *tag,
                 int mem, void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_encrypt");
     return run_call(ctx, key, key_len, iv, iv_len, aad, aad_len, pt, len, ct, tag, false, mem, stream);
 }
 
@@ -967,6 +972,7 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const u
                        const uint8_t *aad, size_t aad_len, const uint8_t *ct, size_t len, const uint8_t *tag,
                        uint8_t *pt, int mem, void *stream)
 {
+    gcmgpu::TraceRange trace_("gcm_decrypt_verify");
     return run_call(ctx, key, key_len, iv, iv_len, aad, aad_len, ct, len, pt, const_cast<uint8_t *>(tag), true,
                     mem, stream);
 }

@@ -8,9 +8,22 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "gcm_internal.h"
 #include "gcmgpu.h"
+
+namespace gcmgpu {
+// A named NVTX range over a scope: the library's public calls and the
+// server's waves show up by name in a profiler timeline (a no-op unless a
+// tool is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+}  // namespace gcmgpu
 
 struct gcm_ctx {
     int device = 0;

@@ -360,7 +360,11 @@ void worker_loop(gcm_server *S)
                 S->slot_busy[slot] = true;
             }
             const uint64_t th0 = now_ns();
-            const int lrc = launch_wave(S, w);
+            int lrc;
+            {
+                gcmgpu::TraceRange trace_("gcm_server wave launch");
+                lrc = launch_wave(S, w);
+            }
             S->t_launch_host_ms += (now_ns() - th0) / 1e6;
             if (lrc != GCM_OK) {
                 std::lock_guard<std::mutex> lk(S->mu);

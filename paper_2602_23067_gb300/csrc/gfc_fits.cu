@@ -871,6 +871,7 @@ int gfc_fits_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uin
                      const uint8_t *iv12, uint8_t *iv_out, uint8_t *tag_out, int aad_mode, int mem, void *stream,
                      gfc_result *out)
 {
+    gcmgpu::TraceRange trace_("gfc_fits_encrypt");
     return fits_call(ctx, false, key, key_len, fits, fits_len, iv12, iv_out, nullptr, tag_out, aad_mode, mem,
                      stream, out);
 }
@@ -879,6 +880,7 @@ int gfc_fits_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len, co
                             const uint8_t *iv12, const uint8_t *tag, int aad_mode, int mem, void *stream,
                             gfc_result *out)
 {
+    gcmgpu::TraceRange trace_("gfc_fits_decrypt_verify");
     return fits_call(ctx, true, key, key_len, fits_enc, len, iv12, nullptr, tag, nullptr, aad_mode, mem, stream,
                      out);
 }
@@ -887,6 +889,7 @@ int gfc_container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, 
                           size_t key_d_len, const uint8_t *fits, size_t fits_len, const uint8_t *nonce_h,
                           const uint8_t *nonce_d, int mem, void *stream, gfc_result *out)
 {
+    gcmgpu::TraceRange trace_("gfc_container_encrypt");
     return container_encrypt(ctx, key_h, key_h_len, key_d, key_d_len, fits, fits_len, nonce_h, nonce_d, mem, stream,
                              out);
 }
@@ -894,6 +897,7 @@ int gfc_container_encrypt(gcm_ctx *ctx, const uint8_t *key_h, size_t key_h_len, 
 int gfc_decrypt_frame(gcm_ctx *ctx, const uint8_t *container, size_t len, const uint8_t *key_h, size_t key_h_len,
                       const uint8_t *key_d, size_t key_d_len, int mem, void *stream, gfc_result *out)
 {
+    gcmgpu::TraceRange trace_("gfc_decrypt_frame");
     return decrypt_frame(ctx, container, len, key_h, key_h_len, key_d, key_d_len, mem, stream, out);
 }
 

@@ -222,3 +222,26 @@ def test_invalid_arguments(torch_cuda, ctx):
     with pytest.raises(GcmError) as e:
         ctx.encrypt_device(bytes(16), bytes(12), None, p[1:33], ct=torch.zeros(32, dtype=torch.uint8, device="cuda"))
     assert e.value.code == -7
+
+
+def test_hbm_budget_refuses_scratch(torch_cuda):
+    # An allocation failure made on the host side: a context whose HBM
+    # budget cannot hold one call's scratch refuses the call with
+    # GCM_ERR_NO_MEMORY (-4) and stays usable; an unlimited context then
+    # gives the oracle's result for the same inputs.
+    from paper_2602_23067_gb300 import Context, GcmError
+
+    torch = torch_cuda
+    key, iv = bytes(range(16)), bytes(12)
+    pt = workloads.random_bytes(77, 1 << 16).tobytes()
+    p = torch.frombuffer(bytearray(pt), dtype=torch.uint8).cuda()
+    with Context(0, hbm_budget_bytes=4096) as small:
+        for _ in range(2):
+            with pytest.raises(GcmError) as e:
+                small.encrypt_device(key, iv, None, p)
+            assert e.value.code == -4
+    with Context(0) as ctx:
+        ct, tag = ctx.encrypt_device(key, iv, None, p)
+        torch.cuda.synchronize()
+        ref_ct, ref_tag = oracle.gcm_encrypt(key, iv, b"", pt)
+        assert bytes(ct.cpu().numpy()) == ref_ct and bytes(tag.cpu().numpy()) == ref_tag
