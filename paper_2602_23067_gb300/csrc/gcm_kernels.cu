@@ -927,9 +927,13 @@ __device__ __forceinline__ void batch_tile(uint8_t *smem, const MsgView &v, cons
 // The CTA that finishes a message's last tile combines its partials (the
 // same right-to-left tree as combine_kernel, inside one CTA) and writes the
 // tag, or the verdict for decryption.
-__device__ void batch_combine(const BatchMsg &m, bool dec)
+// Levels with few products give each product to a whole warp
+// (gf_mul_warp, scratch in smem at SM_WSCR), which has a much shorter
+// latency than one thread's multiply; so does the tag's product.
+__device__ void batch_combine(uint8_t *smem, const BatchMsg &m, bool dec)
 {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+    uint64_t *wscr = reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp;
     uint64_t cnt = m.K;
     int level = 0;
     gf128 *src = m.partials;
@@ -938,7 +942,10 @@ __device__ void batch_combine(const BatchMsg &m, bool dec)
     while (cnt > 1) {
         const uint64_t half = (cnt + 1) / 2;
         const gf128 mult = m.km->h2k[BATCH_TILE_LOG2 + level];
-        for (uint64_t g = t; g < half; g += blockDim.x) {
+        const bool by_warp = half <= (uint64_t)nwarps * 4;
+        const uint64_t first = by_warp ? (uint64_t)warp : (uint64_t)t;
+        const uint64_t step = by_warp ? (uint64_t)nwarps : (uint64_t)blockDim.x;
+        for (uint64_t g = first; g < half; g += step) {
             const uint64_t ri = 2 * g, li = 2 * g + 1;
             gf128 right, left;
             const gf128 *pr = reversed ? &src[cnt - 1 - ri] : &src[ri];
@@ -947,9 +954,10 @@ __device__ void batch_combine(const BatchMsg &m, bool dec)
             if (li < cnt) {
                 const gf128 *pl = reversed ? &src[cnt - 1 - li] : &src[li];
                 for (int k = 0; k < 4; k++) left.w[k] = __ldcg(&pl->w[k]);
-                val = gf_xor(gf_mul(left, mult), right);
+                val = gf_xor(by_warp ? gf_mul_warp(left, mult, wscr) : gf_mul(left, mult), right);
             }
-            for (int k = 0; k < 4; k++) __stcg(&dst[g].w[k], val.w[k]);
+            if (!by_warp || lane == 0)
+                for (int k = 0; k < 4; k++) __stcg(&dst[g].w[k], val.w[k]);
         }
         __threadfence_block();
         __syncthreads();
@@ -960,33 +968,33 @@ __device__ void batch_combine(const BatchMsg &m, bool dec)
         cnt = half;
         level++;
     }
-    if (t == 0) {
-        gf128 s = gf_zero();
-        if (cnt == 1)
-            for (int k = 0; k < 4; k++) s.w[k] = __ldcg(&src[0].w[k]);
-        gf128 lb;
-        const uint64_t abits = m.aad_len * 8u, cbits = m.len * 8u;
-        lb.w[0] = (uint32_t)(abits >> 32);
-        lb.w[1] = (uint32_t)abits;
-        lb.w[2] = (uint32_t)(cbits >> 32);
-        lb.w[3] = (uint32_t)cbits;
-        const gf128 gh = gf_mul(gf_xor(s, lb), m.km->H);
-        const uint4 gm = gf_to_mem(gh);
-        const uint32_t tw[4] = {gm.x ^ m.mm->ej0[0], gm.y ^ m.mm->ej0[1], gm.z ^ m.mm->ej0[2], gm.w ^ m.mm->ej0[3]};
-        uint32_t diff = 0;
-        for (int b = 0; b < 16; b++) {
-            const uint8_t tb = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
-            if (dec)
-                diff |= (uint32_t)(tb ^ m.tag[b]);
-            else
-                m.tag[b] = tb;
-        }
-        *m.status = dec ? (diff ? -3 : 0) : 0;
-        if (m.t_done) {
-            uint64_t now;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-            *m.t_done = now;
-        }
+    if (warp != 0) return;
+    gf128 s = gf_zero();
+    if (cnt == 1)
+        for (int k = 0; k < 4; k++) s.w[k] = __ldcg(&src[0].w[k]);
+    gf128 lb;
+    const uint64_t abits = m.aad_len * 8u, cbits = m.len * 8u;
+    lb.w[0] = (uint32_t)(abits >> 32);
+    lb.w[1] = (uint32_t)abits;
+    lb.w[2] = (uint32_t)(cbits >> 32);
+    lb.w[3] = (uint32_t)cbits;
+    const gf128 gh = gf_mul_warp(gf_xor(s, lb), m.km->H, wscr);
+    if (lane != 0) return;
+    const uint4 gm = gf_to_mem(gh);
+    const uint32_t tw[4] = {gm.x ^ m.mm->ej0[0], gm.y ^ m.mm->ej0[1], gm.z ^ m.mm->ej0[2], gm.w ^ m.mm->ej0[3]};
+    uint32_t diff = 0;
+    for (int b = 0; b < 16; b++) {
+        const uint8_t tb = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
+        if (dec)
+            diff |= (uint32_t)(tb ^ m.tag[b]);
+        else
+            m.tag[b] = tb;
+    }
+    *m.status = dec ? (diff ? -3 : 0) : 0;
+    if (m.t_done) {
+        uint64_t now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        *m.t_done = now;
     }
 }
 
@@ -1073,7 +1081,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         __syncthreads();
         if (s_last) {
             __threadfence();
-            batch_combine(bm, bm.dec != 0);
+            batch_combine(smem, bm, bm.dec != 0);
         }
     }
 }
@@ -1170,37 +1178,60 @@ __global__ void __launch_bounds__(512) combine_kernel(const __grid_constant__ Kc
     // larger ones go through the global scratch.  Levels with many products
     // give one product to each thread; levels with few give each product to
     // a whole warp (gf_mul_warp), which has a much shorter latency.
+    // Everything the serial path reads -- the partials (up to 1024), the
+    // multipliers H^(2^(tile_log2 + level)), H, the round keys and tables of
+    // E_K(J0) -- is staged into shared memory first, in one parallel step,
+    // and E_K(J0) is computed by the last warp while the others run the tree.
     __shared__ gf128 sbuf[2][1024];
     __shared__ uint64_t wscr[16][16];
     __shared__ uint32_t stab[1024];
     __shared__ uint8_t ssbox[256];
+    __shared__ uint32_t srk[60];
+    __shared__ gf128 smult[H2K_COUNT];
+    __shared__ gf128 sH;
+    __shared__ uint32_t sej0[4];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
     const KeyMat *km = p.km;
-    if (p.ej0_from_j0) {
+    const bool aes_warp = p.ej0_from_j0 && !p.raw;  // the last warp computes E_K(J0)
+    const int tree_warps = aes_warp ? nwarps - 1 : nwarps;
+    const uint64_t K = p.K;
+    if (aes_warp) {
         for (int i = t; i < 1024; i += blockDim.x) stab[i] = __ldg(&p.tabs->ttab[i]);
         for (int i = t; i < 256; i += blockDim.x) ssbox[i] = __ldg(&p.tabs->sbox[i]);
+        if (t < 60) srk[t] = __ldg(&km->rk[t]);
+    } else if (!p.raw && t < 4) {
+        sej0[t] = __ldg(&p.mm->ej0[t]);
     }
-    uint64_t cnt = p.K;
+    if (t >= 64 && t < 64 + H2K_COUNT && (uint32_t)(t - 64) + p.tile_log2 < (uint32_t)H2K_COUNT)
+        smult[t - 64] = km->h2k[p.tile_log2 + (t - 64)];
+    if (t == 128) sH = km->H;
+    const bool staged = K <= 1024;
+    if (staged)
+        for (uint64_t i = t; i < K; i += blockDim.x) sbuf[1][i] = p.partials[i];
+    __syncthreads();
+    if (aes_warp && warp == nwarps - 1 && lane == 0) aes_block_tt(srk, (int)km->nr, stab, ssbox, p.j0, sej0);
+
+    uint64_t cnt = K;
     int level = 0;
     // Level 0 reads the partials right to left (index g counts tiles from
     // the end of the sequence), so every right-hand operand is a full group
     // of 2^level tiles and its multiplier is exactly H^(2^(tile_log2+level)).
-    const gf128 *src = p.partials;
+    const gf128 *src = staged ? sbuf[1] : p.partials;
     bool reversed = true;
     int flip = 0;
     while (cnt > 1) {
         const uint64_t half = (cnt + 1) / 2;
-        const gf128 mult = km->h2k[p.tile_log2 + level];
+        const gf128 mult = smult[level];
         gf128 *dst = (half <= 1024) ? sbuf[flip] : ((src == p.scratch) ? p.partials : p.scratch);
-        if (half > (uint64_t)nwarps * 4) {
+        if (half > (uint64_t)tree_warps * 4) {
             for (uint64_t g = t; g < half; g += blockDim.x) {
                 const uint64_t ri = 2 * g, li = 2 * g + 1;
                 gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
                 if (li < cnt) v = gf_xor(gf_mul(reversed ? src[cnt - 1 - li] : src[li], mult), v);
                 dst[g] = v;
             }
-        } else {
-            for (uint64_t g = warp; g < half; g += nwarps) {
+        } else if (warp < tree_warps) {
+            for (uint64_t g = warp; g < half; g += tree_warps) {
                 const uint64_t ri = 2 * g, li = 2 * g + 1;
                 gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
                 if (li < cnt) v = gf_xor(gf_mul_warp(reversed ? src[cnt - 1 - li] : src[li], mult, wscr[warp]), v);
@@ -1214,12 +1245,13 @@ __global__ void __launch_bounds__(512) combine_kernel(const __grid_constant__ Kc
         cnt = half;
         level++;
     }
+    __syncthreads();  // E_K(J0) is in sej0 (also when there was no tree level)
     if (p.dsums) {
         // DATASUM: ones' complement total of the tile partials (each < 2^32,
         // so a 64-bit sum cannot overflow for any supported length).
         __shared__ uint64_t dpart[16];
         uint64_t acc = 0;
-        for (uint64_t i = t; i < p.K; i += blockDim.x) acc += p.dsums[i];
+        for (uint64_t i = t; i < K; i += blockDim.x) acc += p.dsums[i];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
         if (lane == 0) dpart[warp] = acc;
@@ -1239,17 +1271,12 @@ __global__ void __launch_bounds__(512) combine_kernel(const __grid_constant__ Kc
     lb.w[1] = (uint32_t)abits;
     lb.w[2] = (uint32_t)(cbits >> 32);
     lb.w[3] = (uint32_t)cbits;
-    const gf128 gh = gf_mul_warp(gf_xor(s, lb), km->H, wscr[0]);
+    const gf128 gh = gf_mul_warp(gf_xor(s, lb), sH, wscr[0]);
     if (lane != 0) return;
     const uint4 gm = gf_to_mem(gh);
     uint32_t ej0[4] = {0u, 0u, 0u, 0u};
-    if (!p.raw) {
-        if (p.ej0_from_j0) {
-            aes_block_tt(km->rk, (int)km->nr, stab, ssbox, p.j0, ej0);
-        } else {
-            for (int i = 0; i < 4; i++) ej0[i] = p.mm->ej0[i];
-        }
-    }
+    if (!p.raw)
+        for (int i = 0; i < 4; i++) ej0[i] = sej0[i];
     const uint32_t tw[4] = {gm.x ^ ej0[0], gm.y ^ ej0[1], gm.z ^ ej0[2], gm.w ^ ej0[3]};
     if (p.tag_out)
         for (int b = 0; b < 16; b++) p.tag_out[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
