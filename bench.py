@@ -94,12 +94,40 @@ def sm_max_mhz():
         return 2070.0, "nominal GB300 maximum SM clock"
 
 
+def strip_c_comments(src):
+    """C/C++ source with comments removed and whitespace runs collapsed, so
+    that a comment-only edit leaves the code identity unchanged."""
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i]
+        if c == '"' or c == "'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash():
+    """Identity of the fused kernel's code (comments excluded): the files the
+    kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2602_23067_gb300", "csrc")
     for name in ("gcm_kernels.cu", "gcm_device.cuh", "gcm_internal.h"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(strip_c_comments(f.read()).encode())
     return h.hexdigest()
 
 

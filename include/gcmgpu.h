@@ -5,7 +5,7 @@
  * (NIST SP 800-38D over the FIPS-197 block cipher) as adopted by the paper
  * "GpuFitsCrypt" (Sec. 3.2.1): the AES-CTR keystream fused, in one pass over
  * the data, with GHASH recast as the paper's parallel reduction (Sec. 3.3.1,
- * Eq. 1 and Fig. 2b; Sec. 5.2.1-5.2.3): per-chunk Horner, a device table of
+ * Eq. 1 and Fig. 3b; Sec. 5.2.1-5.2.3): per-chunk Horner, a device table of
  * powers of H, and a log-depth combination of chunk partials.  The session
  * object mirrors the paper's context API (Table "Core functions",
  * gfc_context_create / gfc_context_destroy) and the FITS entry points follow
@@ -124,7 +124,7 @@ int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
 
 /* Tile size of the single-message calls.  The fused pass splits the GHASH
  * input sequence A || C into tiles of 2^t 16-byte blocks (the paper's chunks,
- * Sec. 5.2.3 map phase); any t gives the same ciphertext and tag.  By
+ * Sec. 5.2.2 map phase); any t gives the same ciphertext and tag.  By
  * default t comes from the context's tuning table (on a GB300 with 152 SMs a
  * table measured there with gcm_ctx_autotune is installed at creation),
  * else from a rule (t = 16, lowered down to 9 while there are fewer than 4
@@ -151,8 +151,8 @@ int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2);
 #define GCM_AES_BITSLICED 1
 int gcm_ctx_set_aes_impl(gcm_ctx *ctx, int impl);
 
-/* Autotuner (the analogue of the paper's per-GPU (TS, R) search, Sec. 5.3,
- * Table "Kernel-optimal parameters"): times a GCM encryption of
+/* Autotuner (the analogue of the paper's per-GPU (TS, R) search, Sec. 5.4,
+ * Table 3, "Kernel-optimal parameters"): times a GCM encryption of
  * 16 KiB, 64 KiB, 256 KiB, ... (x4) up to max_bytes (at most 1 GiB) of
  * device-resident zeros with a key of key_len bytes for every tile size
  * 2^9..2^16 blocks, and keeps the fastest per size class: table[c] is the
@@ -193,9 +193,9 @@ int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
 
 /* GHASH alone (SP 800-38D Sec. 6.4 / Algorithm 2 over A || 0^v || C || 0^u ||
  * [len(A)]_64 || [len(C)]_64, with H = E_K(0^128); the paper's GHASH-only
- * throughput measurement, Sec. 5.2.3).  Runs the same parallel reduction as
- * the fused pass -- per-chunk Horner, H-power table, log-depth combine
- * (Sec. 3.3.2, Fig. 2) -- but no AES on the payload and no payload output.
+ * throughput measurement, Sec. 5.4, Table 5).  Runs the same parallel
+ * reduction as the fused pass -- per-chunk Horner, H-power table,
+ * log-depth combine (Sec. 3.3.1, Fig. 3b) -- but no AES on the payload and no payload output.
  * out16 receives the 16-byte GHASH value S, so that the GCM tag of the same
  * (A, C) is S xor E_K(J0).  aad, data and out16 are DEVICE pointers (data
  * 16-byte aligned); key is a host pointer.  Enqueues on `stream` and

@@ -8,7 +8,7 @@ may import it.  The product path never imports it; the two share no code.
   (NIST SP 800-38D, Algorithms 1-5), built into ``liboracle.so`` with gcc.
 * this module -- a ctypes binding to it, plus plain-Python helpers that
   follow the paper:
-    - ``tree_ghash``: the parallel tree form of GHASH (Sec. 3.3.1, Fig. 2b;
+    - ``tree_ghash``: the parallel tree form of GHASH (Sec. 3.3.1, Fig. 3b;
       Sec. 5.2.1-5.2.2), used only to pin the regrouping identity that the
       GPU relies on.  Product parity is always checked against the serial
       GHASH of SP 800-38D.
@@ -163,7 +163,7 @@ def ghash(h: bytes, x: bytes) -> bytes:
 
 def chunk_partial(h: bytes, blocks: Sequence[bytes]) -> bytes:
     """Horner over one chunk: sum_j X_j * H^(m-j+1), j = 1..m (the map phase
-    of the paper's two-phase GHASH, Sec. 5.2.3, with the trailing factor H
+    of the paper's two-phase GHASH, Sec. 5.2.2, with the trailing factor H
     kept inside each partial)."""
     y = ZERO
     for blk in blocks:
@@ -173,7 +173,7 @@ def chunk_partial(h: bytes, blocks: Sequence[bytes]) -> bytes:
 
 def combine(h: bytes, left: bytes, right: bytes, right_blocks: int) -> bytes:
     """Combine(L, R) = L * H^(#blocks of R) xor R: joins the partials of two
-    adjacent segments (the paper's tree step, Fig. 2b, where the power of H
+    adjacent segments (the paper's tree step, Fig. 3b, where the power of H
     jumps the gap left by the right-hand segment)."""
     return xor16(gf_mul(left, gf_pow(h, right_blocks)), right)
 
@@ -181,7 +181,7 @@ def combine(h: bytes, left: bytes, right: bytes, right_blocks: int) -> bytes:
 def tree_ghash(h: bytes, x: bytes, cuts: Iterable[int]) -> bytes:
     """GHASH computed the parallel way: split the block sequence at ``cuts``
     (block indices), Horner inside each chunk, then a balanced pairwise tree
-    of ``combine`` steps over the chunk partials (Sec. 3.3.1, Fig. 2b)."""
+    of ``combine`` steps over the chunk partials (Sec. 3.3.1, Fig. 3b)."""
     n = len(x) // 16
     blocks = [x[16 * i: 16 * i + 16] for i in range(n)]
     edges = [0] + sorted(set(c for c in cuts if 0 < c < n)) + [n]
@@ -202,14 +202,14 @@ def tree_ghash(h: bytes, x: bytes, cuts: Iterable[int]) -> bytes:
 
 
 def tree_ghash_fig2b(h: bytes, x: bytes) -> bytes:
-    """The exact shape drawn in Fig. 2b for a power-of-two block count:
+    """The exact shape drawn in Fig. 3b for a power-of-two block count:
     partials omit the trailing H, level k joins pairs with H^(2^k), and one
     final multiplication by H closes the tree."""
     n = len(x) // 16
     if n == 0:
         return ZERO
     if n & (n - 1):
-        raise ValueError("Fig. 2b shape needs a power-of-two block count")
+        raise ValueError("Fig. 3b shape needs a power-of-two block count")
     level = [x[16 * i: 16 * i + 16] for i in range(n)]
     k = 0
     while len(level) > 1:

@@ -1,7 +1,7 @@
 // gcm_kernels.cu -- the AES-GCM hot path on sm_103a.
 //
 // Kernels (one pass over the payload; the paper's CTR kernel and GHASH map
-// kernel, Sec. 3.3.2 and 5.2.3, are fused into KF):
+// kernel, Sec. 3.3.2 and 5.2.2, are fused into KF):
 //   build_tables  once per context: S-box from GF(2^8) and the four AES
 //                 round tables T0..T3 (FIPS-197 sec. 5.1).
 //   KS  key_setup per key/message: key expansion (FIPS-197 sec. 5.2),
@@ -11,12 +11,12 @@
 //   KF  fused     AES-CTR keystream + XOR (geometry-agnostic counters,
 //                 Sec. 5.2: block j always uses inc32^(j+1)(J0)) fused with
 //                 the GHASH map: every CTA reduces tiles of the GHASH input
-//                 sequence A||C to 16-byte partials (Sec. 5.2.3, map phase).
+//                 sequence A||C to 16-byte partials (Sec. 5.2.2, map phase).
 //   KF' fused_bs  the same pass with the CTR keystream from bitsliced AES
 //                 (32 blocks per thread; the paper's own AES core is
 //                 bit-sliced, Sec. 5.2), selected per context.
 //   KC  combine   log-depth tree over the tile partials with multipliers
-//                 H^(2^k) (Sec. 3.3.1, Fig. 2b; Sec. 5.2.3 reduce phase),
+//                 H^(2^k) (Sec. 3.3.1, Fig. 3b; Sec. 5.2.2 reduce phase),
 //                 the length block and T = E_K(J0) xor GHASH; for decryption
 //                 the constant-time tag check (Sec. 3.3.2 item 4).
 //   KZ  zero_fill on an authentication failure the output payload is zeroed

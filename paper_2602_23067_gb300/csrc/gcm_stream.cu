@@ -2,7 +2,7 @@
 //
 // The paper overlaps host<->device transfers with the GCM kernels on CUDA
 // streams with pinned buffers (Sec. 3.3.2, "Asynchronous Streams Pipeline";
-// Sec. 5.2.4).  Here every message's GHASH sequence is cut into chunks of
+// Sec. 5.2.3).  Here every message's GHASH sequence is cut into chunks of
 // whole tiles; chunk c is copied into ring slot c mod R on the copy-in
 // stream, processed by the fused kernel (restricted to the chunk's tiles) on
 // the compute stream, and copied back on the copy-out stream, each step

@@ -182,7 +182,7 @@ def test_gf128_powers_add():
 
 
 # --------------------------------------------------------------------------
-# GHASH: serial (Eq. 1) versus the paper's tree (Fig. 2b)
+# GHASH: serial (Eq. 1) versus the paper's tree (Fig. 3b)
 # --------------------------------------------------------------------------
 
 def test_ghash_special_cases():
