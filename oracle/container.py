@@ -3,7 +3,7 @@
 Table "Role-based and temporal access control policies") -- test
 infrastructure only, like the rest of this package.
 
-Layout (the paper fixes the contents; the encodings below are this build's
+Layout (the paper fixes the contents; the encodings below are this library's
 readings where the paper is silent):
 
 * HDU 0, metadata only (NAXIS = 0): NONCE_H, NONCE_D (12-byte nonces, as
