@@ -538,11 +538,11 @@ __device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgVi
 // are aligned to its end (the first tile is the short one; it is treated as
 // the smallest tile of 2^lg >= its length blocks, left-padded with zero
 // blocks).  Warp w owns segment w of the tile (S = 2^lg/16 blocks).  On
-// whole-payload segments the warp walks windows of 32 counters aligned to
-// multiples of 32, so a window never crosses a 256-counter group: rounds 1
-// and 2 of AES then need only the lookups that depend on the counter's low
-// byte (counter-mode caching; the rest are per-group constants computed
-// once per 256 counters).  Lane l chains the
+// whole-payload segments the warp walks windows of 32 blocks from the
+// segment start (no partial windows).  Rounds 1 and 2 of AES need only the
+// lookups that depend on the counter's low byte (counter-mode caching): the
+// rest are per-lane constants of the lane's 256-counter group, refreshed
+// when its counter enters a new group.  Lane l chains the
 // l-th block of every window through acc <- acc*H^32 xor X and closes the
 // chain with H^e, e = distance of its last block from the segment end; the
 // warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
@@ -581,29 +581,23 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     if (seg_hi > seg_lo) {
         seg_len = (uint32_t)(seg_hi - seg_lo);
         if ((uint64_t)seg_lo >= v.a_blocks && (uint64_t)seg_hi <= v.a_blocks + v.n_full) {
-            // Whole payload blocks: counter-aligned windows of 32.
+            // Whole payload blocks: windows of 32 from the segment start.
             const uint64_t j_lo = (uint64_t)seg_lo - v.a_blocks;
             const uint32_t c_lo = c.ctr0 + 1u + (uint32_t)j_lo;
-            const uint32_t W0 = c_lo & ~31u;
-            const uint32_t nwin = (seg_len + (c_lo & 31u) + 31u) >> 5;
+            const uint32_t nwin = (seg_len + 31u) >> 5;
             const uint4 *in = reinterpret_cast<const uint4 *>(v.in) + j_lo;
             uint4 *out = reinterpret_cast<uint4 *>(v.out) + j_lo;
             // The next window's input is loaded one window ahead, so a load's
             // latency (long when the payload is in host memory across the
             // CPU-GPU link) overlaps a window of AES work.
             uint4 din_next = make_uint4(0u, 0u, 0u, 0u);
-            {
-                const uint32_t d0 = W0 + lane - c_lo;
-                if (d0 < seg_len) din_next = __ldcs(in + d0);
-            }
+            if (lane < seg_len) din_next = __ldcs(in + lane);
             for (uint32_t wi = 0; wi < nwin; wi++) {
-                const uint32_t W = W0 + (wi << 5);
-                const uint32_t d = W + lane - c_lo;
+                const uint32_t d = (wi << 5) + lane;
                 const bool active = d < seg_len;
+                // This lane's counter word (inc32 arithmetic: wraps mod 2^32).
+                const uint32_t ctr = c_lo + d;
                 const uint4 din = din_next;
-                // The offset is formed in 32-bit arithmetic first: for lanes
-                // before the segment start d has wrapped and d + 32 is their
-                // (small) offset in the next window.
                 const uint32_t dn = d + 32u;
                 if (dn < seg_len) din_next = __ldcs(in + dn);
                 if (MODE == MODE_GHASH) {
@@ -616,10 +610,13 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                     }
                     continue;
                 }
-                if ((W >> 8) != gc.grp) {
-                    // Per-group constants of rounds 1-2 (counter bytes 12..14 fixed).
-                    gc.grp = W >> 8;
-                    const uint32_t x3g = bswap32(W) ^ c.rk3;
+                if ((ctr >> 8) != gc.grp) {
+                    // Per-group constants of rounds 1-2 (counter bytes 12..14
+                    // fixed).  A window that straddles a 256-counter boundary
+                    // refreshes only the lanes past it (the others refresh one
+                    // window later): two divergent refreshes per 8 windows.
+                    gc.grp = ctr >> 8;
+                    const uint32_t x3g = bswap32(ctr) ^ c.rk3;
                     const uint32_t u1 = c.K1 ^ LT2(x3g, 2);
                     const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
                     const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
@@ -630,7 +627,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                 }
                 // Round 1 column 0 (the only column that sees counter byte 15),
                 // then round 2 (one varying lookup per column).
-                const uint32_t x15 = ((W & 0xE0u) | lane) ^ c.k15;
+                const uint32_t x15 = (ctr & 0xFFu) ^ c.k15;
                 const uint32_t v0 = c.K0 ^ LT3(x15, 0);
                 uint4 ks = aes_rounds_from3<NR>(t01, t23, L, gc.G0 ^ LT0(v0, 0), gc.G1 ^ LT3(v0, 3),
                                                 gc.G2 ^ LT2(v0, 2), gc.G3 ^ LT1(v0, 1), rk);
