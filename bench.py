@@ -390,14 +390,19 @@ def run_ours(args):
         sampler.start()
         time.sleep(0.25)
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    # One event between consecutive steps (no extra device work), so that
+    # the per-step distribution (median, spread; the paper's protocol,
+    # Sec. 5.3.1) comes with the total.
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
         step()
-    e1.record(stream)
+        evs[i + 1].record(stream)
     barrier()
     clocks = sampler.stop() if sampler else None
+    e0, e1 = evs[0], evs[-1]
     ms = e0.elapsed_time(e1)
+    step_ms = np.array([evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)])
     prof = _native.gcm_profile_read(ctx.handle, reset=True)
     _native.gcm_profile_enable(ctx.handle, False)
     ms = max_over_ranks(ms, dist)
@@ -585,6 +590,9 @@ def run_ours(args):
         "dtype": "u8",
         "data": "synthetic",
         "config": workload_config(world),
+        "step_ms": {"median": float(np.median(step_ms)), "std": float(np.std(step_ms)),
+                    "min": float(step_ms.min()), "max": float(step_ms.max()),
+                    "what": "device time of each timed step (rank 0), CUDA events between steps"},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -65,3 +65,35 @@ def test_autotune_table_and_parity(torch_cuda):
             assert bytes(tag.cpu().numpy()) == ref_tag and bytes(ct.cpu().numpy()) == ref_ct
         ctx.set_tuning(table)
         ctx.set_tuning(None)
+
+
+@pytest.mark.parametrize("tile_log2", [10, 12])
+def test_segment_start_offsets(torch_cuda, tile_log2):
+    # Whole-payload segments are walked in 32-block windows from the segment
+    # start; a lane takes the AES round-1/2 constants of its own 256-counter
+    # group and refreshes them when its counter enters a new group, so a
+    # window that straddles a group boundary refreshes only some lanes.
+    # AAD of 0..31 blocks moves every segment's first counter through all
+    # residues mod 32, and non-96-bit IVs (J0 from GHASH(IV)) start the
+    # counter word anywhere mod 256 (and let it wrap mod 2^32).
+    from paper_2602_23067_gb300 import Context
+
+    torch = torch_cuda
+    r = random.Random(9600 + tile_log2)
+    n = 3 * (16 << tile_log2) + 37
+    with Context(0) as ctx:
+        ctx.set_tile_log2(tile_log2)
+        for k in range(32):
+            a = 0 if k == 0 else 16 * k - (k % 7)
+            key = bytes(r.getrandbits(8) for _ in range(16 if k % 2 else 32))
+            iv = bytes(r.getrandbits(8) for _ in range(12 if k % 4 < 2 else 8 + 13 * (k % 5)))
+            aad = bytes(r.getrandbits(8) for _ in range(a))
+            pt = workloads.random_bytes(9600 + 64 * tile_log2 + k, n).tobytes()
+            ref_ct, ref_tag = oracle.gcm_encrypt(key, iv, aad, pt)
+            d_aad = dev(torch, aad) if aad else None
+            ct, tag = ctx.encrypt_device(key, iv, d_aad, dev(torch, pt))
+            torch.cuda.synchronize()
+            assert bytes(tag.cpu().numpy()) == ref_tag, (k, len(iv))
+            assert bytes(ct.cpu().numpy()) == ref_ct, (k, len(iv))
+            back = ctx.decrypt_verify_device(key, iv, d_aad, ct, tag)
+            assert bytes(back.cpu().numpy()) == pt, (k, len(iv))
