@@ -198,7 +198,7 @@ def test_ghash_special_cases():
 def test_ghash_tree_equals_serial_for_every_split_small():
     r = random.Random(14)
     h = rnd(r, 16)
-    for n in range(1, 9):
+    for n in range(1, 13):  # all 2^(n-1) ways to cut n blocks into chunks, n <= 12
         x = rnd(r, 16 * n)
         ref = oracle.ghash(h, x)
         for mask in range(1 << (n - 1)):
@@ -293,15 +293,27 @@ def _crypto_gcm(key, iv, aad, pt):
 def test_gcm_against_cryptography_random():
     pytest.importorskip("cryptography")
     r = random.Random(20)
-    for case in range(400):
+    for case in range(10000):
         key = rnd(r, r.choice((16, 24, 32)))
         iv = rnd(r, 12 if r.random() < 0.6 else r.randrange(8, 129))
-        aad = rnd(r, r.choice((0, r.randrange(0, 70), r.randrange(0, 700))))
+        aad = rnd(r, r.choice((0, r.randrange(0, 70), r.randrange(0, 700), r.randrange(0, 4097))))
         pt = rnd(r, r.choice((0, r.randrange(0, 48), r.randrange(0, 3000))))
         ct, tag = oracle.gcm_encrypt(key, iv, aad, pt)
         assert (ct, tag) == _crypto_gcm(key, iv, aad, pt), case
         ok, back = oracle.gcm_decrypt(key, iv, aad, ct, tag)
         assert ok and back == pt
+
+
+def test_gcm_against_cryptography_long_messages():
+    pytest.importorskip("cryptography")
+    r = random.Random(21)
+    for case in range(100):
+        key = rnd(r, r.choice((16, 24, 32)))
+        iv = rnd(r, 12 if r.random() < 0.6 else r.randrange(8, 129))
+        aad = rnd(r, r.randrange(0, 4097))
+        pt = rnd(r, r.randrange(0, 65537))
+        ct, tag = oracle.gcm_encrypt(key, iv, aad, pt)
+        assert (ct, tag) == _crypto_gcm(key, iv, aad, pt), case
 
 
 def test_gcm_against_cryptography_aesgcm_96bit():
