@@ -617,8 +617,7 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     if (e == cudaSuccess) {
         int pageable = 0;
         cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device);
-        const char *force = getenv("GCMGPU_HOST_STAGING");
-        ctx->host_direct = pageable != 0 && !(force && force[0] == '1');
+        ctx->host_direct = pageable != 0;
     }
     if (e == cudaSuccess) e = configure_kernels();
     if (e == cudaSuccess) {
