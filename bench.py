@@ -999,8 +999,29 @@ def run_catalog(args):
         sizes.append(workloads.padded_len(4096 * 4096 * (4 if i % 2 == 0 else 2)))
     offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
     total = int(offs[-1])
-    # The catalog lives in ordinary (pageable) host memory, filled from the GPU.
-    cat = torch.empty(total, dtype=torch.uint8)
+    # The catalog lives in host memory, filled from the GPU: page-locked
+    # (gcm_host_alloc, exact size) by default, or ordinary pageable memory.
+    # Page-locked memory is taken only when the host has room for it.
+    hostbuf = None
+    memory = args.catalog_memory
+    if memory == "pinned":
+        avail = 0
+        try:
+            with open("/proc/meminfo") as f:
+                for ln in f:
+                    if ln.startswith("MemAvailable:"):
+                        avail = int(ln.split()[1]) * 1024
+        except OSError:
+            pass
+        if avail >= total + (16 << 30):
+            from paper_2602_23067_gb300 import HostBuffer
+
+            hostbuf = HostBuffer(total, local)
+            cat = hostbuf.tensor
+        else:
+            memory = "pageable (page-locked requested; %.0f GB available)" % (avail / 1e9)
+    if hostbuf is None:
+        cat = torch.empty(total, dtype=torch.uint8)
     ref_sample = []
     g = torch.Generator(device="cuda")
     g.manual_seed(5)
@@ -1067,12 +1088,16 @@ def run_catalog(args):
         "data": "synthetic",
         "config": {"workload": "catalog_64GiB", "files": 2 * n_pairs, "bytes": total,
                    "files_kind": "alternating 4096x4096 float32 / int16 data units, random headers as AAD",
-                   "host_memory": "pageable (plain CPU tensor)", "in_place": True},
+                   "host_memory": "page-locked (gcm_host_alloc)" if hostbuf is not None else memory,
+                   "in_place": True},
         "catalog": results,
         "e2e": {"value": 2 * total / (best["encrypt_s"] + best["decrypt_s"]) / 1e9, "unit": "GB/s",
                 "h2d_bytes_per_step": 2 * total, "d2h_bytes_per_step": 2 * total},
         "cpu_baseline": cpu,
     }
+    del cat
+    if hostbuf is not None:
+        hostbuf.free()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -1232,6 +1257,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-bytes", type=int, default=8 << 20)
     ap.add_argument("--catalog-pairs", type=int, default=683, help="catalog: float32/int16 file pairs (683 = 64 GiB)")
+    ap.add_argument("--catalog-memory", choices=["pinned", "pageable"], default="pinned",
+                    help="catalog: page-locked host memory (default) or ordinary pageable memory")
     ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog"], default="fits4g",
                     help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages; "
                          "serving: Poisson request stream")

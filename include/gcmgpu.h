@@ -265,6 +265,20 @@ int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
  * mode 2: always stage through device chunk buffers. */
 int gcm_ctx_set_host_access(gcm_ctx *ctx, int mode);
 
+/* Page-locked host memory of exactly `bytes` (cudaHostAlloc, default
+ * flags, made under CUDA device `device`) for GCM_MEM_HOST calls, host
+ * batches and the server.  The GPU reaches page-locked memory through its
+ * own page tables (no per-page address translation over the CPU-GPU link),
+ * and the staged pipeline's copies from it run asynchronously.  The caller
+ * owns the memory and releases it with gcm_host_free.  *out receives the
+ * pointer, or NULL on failure.  Returns GCM_ERR_INVALID_ARG for out == NULL,
+ * bytes == 0 or a bad device, GCM_ERR_NO_MEMORY when the allocation fails. */
+int gcm_host_alloc(int device, size_t bytes, void **out);
+
+/* Releases memory from gcm_host_alloc; p == NULL is a no-op.  Returns
+ * GCM_ERR_CUDA if the runtime refuses the pointer. */
+int gcm_host_free(void *p);
+
 /* Host-mode streaming geometry: chunk_bytes of payload per chunk (rounded
  * to whole tiles) and n_buffers device chunk buffers in the ring (>= 2).
  * Defaults: 256 MiB and 3. */

@@ -124,6 +124,8 @@ SIGNATURES = {
     "gfc_decrypt_frame": (ctypes.c_int, [_VP, _VP, _SZ, _VP, _SZ, _VP, _SZ, ctypes.c_int, _VP,
                                          ctypes.POINTER(GfcResult)]),
     "gcm_noalloc_last_error": (ctypes.c_char_p, []),
+    "gcm_host_alloc": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.POINTER(_VP)]),
+    "gcm_host_free": (ctypes.c_int, [_VP]),
 }
 
 

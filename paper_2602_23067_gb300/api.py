@@ -17,7 +17,7 @@ from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GFC_AA
 __all__ = [
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
     "gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "last_error",
-    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server",
+    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server", "HostBuffer",
 ]
 
 
@@ -453,6 +453,33 @@ class Context:
         result has error_code GCM_ERR_AUTH, warning_code 2 and a zeroed data
         unit (payload suppression)."""
         return self._fits_common(True, key, fits_enc, iv, tag, aad_mode, stream)
+
+
+class HostBuffer:
+    """Page-locked host memory of exactly ``nbytes`` from gcm_host_alloc, for
+    GCM_MEM_HOST calls, host batches and the server.  ``ptr`` is the address
+    and ``tensor`` a uint8 CPU tensor over it (valid until ``free``)."""
+
+    def __init__(self, nbytes: int, device: int = 0):
+        import torch
+
+        p = ctypes.c_void_p()
+        check(lib.gcm_host_alloc(device, nbytes, ctypes.byref(p)))
+        self.ptr = int(p.value)
+        self.nbytes = nbytes
+        self.tensor = torch.frombuffer((ctypes.c_uint8 * nbytes).from_address(self.ptr), dtype=torch.uint8)
+
+    def free(self) -> None:
+        if self.ptr:
+            self.tensor = None
+            check(lib.gcm_host_free(ctypes.c_void_p(self.ptr)))
+            self.ptr = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
 
 
 class _Raw:

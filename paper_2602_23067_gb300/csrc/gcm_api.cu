@@ -650,6 +650,35 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
     return GCM_OK;
 }
 
+int gcm_host_alloc(int device, size_t bytes, void **out)
+{
+    if (!out) return fail(GCM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (bytes == 0) return fail(GCM_ERR_INVALID_ARG, "bytes must be positive");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(GCM_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(GCM_ERR_CUDA, "cannot select the device");
+    void *p = nullptr;
+    e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GCM_ERR_NO_MEMORY, "page-locked host allocation failed");
+    }
+    *out = p;
+    return GCM_OK;
+}
+
+int gcm_host_free(void *p)
+{
+    if (!p) return GCM_OK;
+    cudaError_t e = cudaFreeHost(p);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFreeHost");
+    return GCM_OK;
+}
+
 int gcm_ctx_set_host_access(gcm_ctx *ctx, int mode)
 {
     if (!ctx) return fail(GCM_ERR_INVALID_ARG, "context is NULL");

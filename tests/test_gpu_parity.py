@@ -200,6 +200,29 @@ def test_host_mode(torch_cuda, ctx, host_access):
     ctx.set_host_access(0)
 
 
+@pytest.mark.parametrize("host_access", [0, 2])
+def test_host_mode_page_locked(torch_cuda, ctx, host_access):
+    # Buffers from gcm_host_alloc (exact size, page-locked), in place: the
+    # kernels on the host memory directly (0) and the staged copy pipeline (2).
+    from paper_2602_23067_gb300 import HostBuffer
+
+    torch = torch_cuda
+    ctx.set_host_access(host_access)
+    r = random.Random(7100 + host_access)
+    key, iv, aad = rnd(r, 16), rnd(r, 60), rnd(r, 100)
+    n = 1000003
+    pt = workloads.random_bytes(7101, n).tobytes()
+    ref_ct, ref_tag = oracle.gcm_encrypt(key, iv, aad, pt)
+    with HostBuffer(n) as hb:
+        assert hb.tensor.numel() == n and hb.ptr % 16 == 0
+        hb.tensor.copy_(torch.frombuffer(bytearray(pt), dtype=torch.uint8))
+        _, tag = ctx.encrypt_host(key, iv, aad, hb.tensor, ct=hb.tensor)
+        assert tag == ref_tag and bytes(hb.tensor.numpy()) == ref_ct
+        ctx.decrypt_verify_host(key, iv, aad, hb.tensor, tag, pt=hb.tensor)
+        assert bytes(hb.tensor.numpy()) == pt
+    ctx.set_host_access(0)
+
+
 def test_fits_shaped_file(torch_cuda, ctx):
     # header records in clear as AAD, 2880-padded data unit as payload
     f = workloads.fits_file_host(8, 300, 200, n_sources=20)
