@@ -463,9 +463,13 @@ __device__ __forceinline__ void stage_segment_factors(uint8_t *smem, const KeyMa
     if (lane == 0) segf[warp] = km->segf[tile_log2 - SEGF_MIN_LOG2][warp];
 }
 
-// Per-CTA cache of the counter-group constants of AES round 2.
+// Per-lane cache of the counter-group constants of AES round 2: G0..G3 for
+// the lane's 256-counter group, and P0..P3, their parts that depend only on
+// counter bytes 12 and 13 (and round-key words 8..11), for its 65536-counter
+// group.
 struct GroupCache {
     uint32_t grp, G0, G1, G2, G3;
+    uint32_t grp_hi, P0, P1, P2, P3;
 };
 
 // A segment that touches the AAD or the final partial block: lane l takes
@@ -548,8 +552,11 @@ __device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgVi
 // warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
 // reduces the 16 warp partials into v.partials[tile].
 // Needs the round tables, the message's GHASH table and segment factors in
-// shared memory; contains two __syncthreads.
-template <int NR, int MODE = MODE_GCM>
+// shared memory; contains two __syncthreads.  HI_CACHE keeps the counter-
+// byte-12/13 terms of the group constants across groups (fewer lookups per
+// refresh, five more registers; the batched kernel, which has none to
+// spare, recomputes them).
+template <int NR, int MODE = MODE_GCM, bool HI_CACHE = true>
 __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const MsgConst &c, const uint32_t *rk,
                                           const LaneConst &L, uint64_t tile, GroupCache &gc)
 {
@@ -615,15 +622,25 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                     // fixed).  A window that straddles a 256-counter boundary
                     // refreshes only the lanes past it (the others refresh one
                     // window later): two divergent refreshes per 8 windows.
+                    // Between consecutive groups only counter byte 14 (u1)
+                    // changes, so the terms of bytes 12 and 13 (u2, u3) are
+                    // kept in P0..P3 and rebuilt once per 65536 counters.
                     gc.grp = ctr >> 8;
                     const uint32_t x3g = bswap32(ctr) ^ c.rk3;
+                    if (!HI_CACHE || (ctr >> 16) != gc.grp_hi) {
+                        gc.grp_hi = ctr >> 16;
+                        const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
+                        const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
+                        gc.P0 = LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
+                        gc.P1 = LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
+                        gc.P2 = LT0(u2, 0) ^ LT1(u3, 1) ^ __ldg(&km->rk[10]);
+                        gc.P3 = LT0(u3, 0) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
+                    }
                     const uint32_t u1 = c.K1 ^ LT2(x3g, 2);
-                    const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
-                    const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
-                    gc.G0 = LT1(u1, 1) ^ LT2(u2, 2) ^ LT3(u3, 3) ^ __ldg(&km->rk[8]);
-                    gc.G1 = LT0(u1, 0) ^ LT1(u2, 1) ^ LT2(u3, 2) ^ __ldg(&km->rk[9]);
-                    gc.G2 = LT0(u2, 0) ^ LT1(u3, 1) ^ LT3(u1, 3) ^ __ldg(&km->rk[10]);
-                    gc.G3 = LT0(u3, 0) ^ LT2(u1, 2) ^ LT3(u2, 3) ^ __ldg(&km->rk[11]);
+                    gc.G0 = gc.P0 ^ LT1(u1, 1);
+                    gc.G1 = gc.P1 ^ LT0(u1, 0);
+                    gc.G2 = gc.P2 ^ LT3(u1, 3);
+                    gc.G3 = gc.P3 ^ LT2(u1, 2);
                 }
                 // Round 1 column 0 (the only column that sees counter byte 15),
                 // then round 2 (one varying lookup per column).
@@ -733,8 +750,9 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
                                   : make_msg_const(t01, t23, L, p.km, __ldg(&p.mm->j0[0]), __ldg(&p.mm->j0[1]),
                                                    __ldg(&p.mm->j0[2]), __ldg(&p.mm->j0[3]));
     GroupCache gc;
-    gc.grp = 0xFFFFFFFFu;
+    gc.grp = gc.grp_hi = 0xFFFFFFFFu;  // no counter group matches (ctr >> 8 < 2^24)
     gc.G0 = gc.G1 = gc.G2 = gc.G3 = 0u;
+    gc.P0 = gc.P1 = gc.P2 = gc.P3 = 0u;
     for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
         tile_body<NR, MODE>(smem, v, c, rk, L, tile, gc);
 }
@@ -918,7 +936,7 @@ __device__ __forceinline__ void batch_tile(uint8_t *smem, const MsgView &v, cons
     for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&v.km->rk[i]);
     const MsgConst c = make_msg_const(t01, t23, L, v.km, __ldg(&v.mm->j0[0]), __ldg(&v.mm->j0[1]),
                                       __ldg(&v.mm->j0[2]), __ldg(&v.mm->j0[3]));
-    tile_body<NR>(smem, v, c, rk, L, tile, gc);
+    tile_body<NR, MODE_GCM, false>(smem, v, c, rk, L, tile, gc);
 }
 
 // The CTA that finishes a message's last tile combines its partials (the
@@ -1058,7 +1076,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
             if (lane == 0)
                 reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[BATCH_TILE_LOG2 - SEGF_MIN_LOG2][warp];
             cur = mi;
-            gc.grp = 0xFFFFFFFFu;
+            gc.grp = gc.grp_hi = 0xFFFFFFFFu;  // the constants belong to the previous message
             __syncthreads();
         }
         const uint64_t tile = item - bm.item_base;
