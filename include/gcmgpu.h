@@ -63,7 +63,12 @@ typedef enum {
 } gcm_mem;
 
 /* Opaque session: device scratch pools, streams, the key cache and the HBM
- * budget.  One context serves one device. */
+ * budget.  One context serves one device.  Calls on one context may come
+ * from several host threads at once, each on its own stream: the key cache,
+ * the scratch accounting and the profiling state are guarded inside the
+ * context, and per-call scratch is stream-ordered.  Changing a setting
+ * (gcm_ctx_set_*) while calls are in flight is not supported, except as
+ * gcm_ctx_set_key_cache documents. */
 typedef struct gcm_ctx gcm_ctx;
 
 /* Creates a session on CUDA device `device`.  hbm_budget_bytes caps the
