@@ -93,8 +93,11 @@ const char *gcm_last_error(void);
  *   pt/len      : plaintext;  ct receives len bytes of ciphertext.
  *   tag         : receives the 16-byte tag T = E_K(J0) xor GHASH_H(A, C).
  * Device mode: returns once the work is enqueued on `stream`.
- * Host mode:   streams the buffers through device chunk buffers (see
- *              gcm_batch) and returns when done; `stream` is not used. */
+ * Host mode:   returns when done.  Where the device reads host memory
+ *              directly (gcm_ctx_set_host_access) and pt/ct are 16-byte
+ *              aligned, the kernels run on the host buffers on `stream`;
+ *              otherwise the buffers stream through the context's device
+ *              chunk buffers (see gcm_batch) and `stream` is not used. */
 int gcm_encrypt(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
                 const uint8_t *iv, size_t iv_len,
                 const uint8_t *aad, size_t aad_len,

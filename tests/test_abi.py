@@ -8,7 +8,7 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-DECL = re.compile(r"^\s*(?:const\s+)?(?:int|void|char|size_t|int32_t|uint32_t|gcm_status)\s*\**\s*(g(?:cm|fc)_\w+)\s*\(",
+DECL = re.compile(r"^\s*(?:const\s+)?(?:int|void|char|size_t|int32_t|uint32_t|uint64_t|gcm_status)\s*\**\s*(g(?:cm|fc)_\w+)\s*\(",
                   re.M)
 
 
@@ -62,3 +62,22 @@ def test_errors_without_a_device_are_reported_not_raised(native):
     rc = native.lib.gcm_encrypt(None, None, 16, None, 12, None, 0, None, 0, None, None, 0, None)
     assert rc == native.GCM_ERR_INVALID_ARG
     assert "NULL" in native.last_error()
+
+
+def build_c_consumer(out_dir):
+    """Compiles tests/abi_consumer.c (C99, warnings as errors) against the
+    header and links it to the library; returns the executable's path."""
+    lib_dir = os.path.join(ROOT, "paper_2602_23067_gb300")
+    exe = os.path.join(out_dir, "abi_consumer")
+    cmd = ["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+           os.path.join(ROOT, "tests", "abi_consumer.c"), "-o", exe, "-L", lib_dir, "-lgcmgpu",
+           "-Wl,-rpath," + lib_dir]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    return exe
+
+
+def test_header_is_plain_c_and_links(native, tmp_path):
+    # The boundary needs no C++ and no Python: a C99 program that includes
+    # the header compiles without warnings and links against the library.
+    assert os.path.exists(build_c_consumer(str(tmp_path)))
