@@ -246,11 +246,15 @@ typedef struct {
  *   messages is one launch.  Messages of different key sizes mix freely.
  *   Items are handed out shortest message first (status stays in the
  *   caller's order), which lowers the median completion time.
- * GCM_MEM_HOST: buffers (ideally pinned) are streamed through a ring of
- *   device chunk buffers: host-to-device copies, the fused kernel and
- *   device-to-host copies of successive chunks overlap on three streams
- *   (the paper's asynchronous stream pipeline, Sec. 3.3.2), so catalogs
- *   larger than device memory pass through a fixed device footprint.
+ * GCM_MEM_HOST: where the device reads host memory directly
+ *   (gcm_ctx_set_host_access) and every message's in/out is 16-byte
+ *   aligned, the same persistent launch runs over the host buffers (page-
+ *   locked ones, e.g. from gcm_host_alloc, are reached fastest).  Otherwise
+ *   the buffers are streamed through a ring of device chunk buffers: host-
+ *   to-device copies, the fused kernel and device-to-host copies of
+ *   successive chunks overlap on three streams (the paper's asynchronous
+ *   stream pipeline, Sec. 3.3.2), so catalogs larger than device memory
+ *   pass through a fixed device footprint.
  * stream: the stream the device-mode launch is ordered on (host mode uses
  *   the context's own streams). */
 int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
