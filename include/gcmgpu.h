@@ -12,9 +12,10 @@
  * its FitsOperationResult convention (same table).
  *
  * Conventions that hold for every call below:
- *   - Every function returns a gcm_status (0 = success, negative = error).
- *     The message of the last error on the calling thread is available
- *     from gcm_last_error().
+ *   - Every function declared to return int returns a gcm_status (0 =
+ *     success, negative = error); the others say what they return.  The
+ *     message of the last error on the calling thread is available from
+ *     gcm_last_error().
  *   - key and iv are always HOST pointers; the library copies them.
  *   - Buffers named "data" (aad, pt, ct, tag) are DEVICE pointers when
  *     mem == GCM_MEM_DEVICE and HOST pointers when mem == GCM_MEM_HOST.
@@ -190,7 +191,7 @@ int gcm_sync(gcm_ctx *ctx, void *stream);
 
 /* CTR keystream XOR alone (SP 800-38D GCTR started at inc32(J0), the
  * ciphertext half of GCM-AE; the paper's CTR kernel, Sec. 3.3.2, and its
- * unauthenticated CTR comparison in Sec. 5).  out = in xor E_K(inc32^i(J0)),
+ * unauthenticated CTR comparison, Sec. 5.4, Table 4).  out = in xor E_K(inc32^i(J0)),
  * byte for byte the ciphertext gcm_encrypt would write; no tag.  Same key
  * and IV rules as gcm_encrypt.  in/out are DEVICE pointers, 16-byte aligned,
  * out may equal in; key and iv are host pointers.  Enqueues on `stream` and
@@ -203,7 +204,8 @@ int gcm_ctr_xor(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
  * [len(A)]_64 || [len(C)]_64, with H = E_K(0^128); the paper's GHASH-only
  * throughput measurement, Sec. 5.4, Table 5).  Runs the same parallel
  * reduction as the fused pass -- per-chunk Horner, H-power table,
- * log-depth combine (Sec. 3.3.1, Fig. 3b) -- but no AES on the payload and no payload output.
+ * log-depth combine (Sec. 3.3.1, Fig. 3b) -- but no AES on the payload
+ * and no payload output.
  * out16 receives the 16-byte GHASH value S, so that the GCM tag of the same
  * (A, C) is S xor E_K(J0).  aad, data and out16 are DEVICE pointers (data
  * 16-byte aligned); key is a host pointer.  Enqueues on `stream` and
