@@ -121,7 +121,7 @@ int gcm_decrypt_verify(gcm_ctx *ctx, const uint8_t *key, size_t key_len,
 /* Sets how many keys the session keeps set up on the device for
  * gcm_encrypt / gcm_decrypt_verify / gcm_ctr_xor / gcm_ghash (default 64;
  * 0 disables the cache).  A call whose key is cached skips the key setup
- * (round keys, H and its power tables, about 67 KB per key) and only derives
+ * (round keys, H and its power tables, 67.4 KiB per key) and only derives
  * J0 and E_K(J0) for its IV; a new key replaces the least recently used entry
  * that no call in flight still reads.  The cache holds key material on the
  * device and the key bytes in host memory until the entry is replaced, the
@@ -303,7 +303,7 @@ int gcm_ctx_set_streaming(gcm_ctx *ctx, size_t chunk_bytes, int n_buffers);
 /* ---------------------------------------------------------------- */
 
 /* Builds a key's material once on the device (round keys, H, powers of H,
- * the GHASH table: about 74 KiB) and returns a handle for server requests.
+ * the GHASH table: 67.4 KiB) and returns a handle for server requests.
  * Register keys before submitting requests that use them. */
 int gcm_key_register(gcm_ctx *ctx, const uint8_t *key, size_t key_len, uint32_t *handle);
 
