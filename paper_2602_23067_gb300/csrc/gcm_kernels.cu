@@ -552,11 +552,8 @@ __device__ __forceinline__ void segment_general(const uint8_t *smem, const MsgVi
 // warp's partial then moves to the tile end with H^((15-w)*S) and the CTA
 // reduces the 16 warp partials into v.partials[tile].
 // Needs the round tables, the message's GHASH table and segment factors in
-// shared memory; contains two __syncthreads.  HI_CACHE keeps the counter-
-// byte-12/13 terms of the group constants across groups (fewer lookups per
-// refresh, five more registers; the batched kernel, which has none to
-// spare, recomputes them).
-template <int NR, int MODE = MODE_GCM, bool HI_CACHE = true>
+// shared memory; contains two __syncthreads.
+template <int NR, int MODE = MODE_GCM>
 __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const MsgConst &c, const uint32_t *rk,
                                           const LaneConst &L, uint64_t tile, GroupCache &gc)
 {
@@ -627,7 +624,7 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                     // kept in P0..P3 and rebuilt once per 65536 counters.
                     gc.grp = ctr >> 8;
                     const uint32_t x3g = bswap32(ctr) ^ c.rk3;
-                    if (!HI_CACHE || (ctr >> 16) != gc.grp_hi) {
+                    if ((ctr >> 16) != gc.grp_hi) {
                         gc.grp_hi = ctr >> 16;
                         const uint32_t u2 = c.K2 ^ LT1(x3g, 1);
                         const uint32_t u3 = c.K3 ^ LT0(x3g, 0);
@@ -936,7 +933,7 @@ __device__ __forceinline__ void batch_tile(uint8_t *smem, const MsgView &v, cons
     for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&v.km->rk[i]);
     const MsgConst c = make_msg_const(t01, t23, L, v.km, __ldg(&v.mm->j0[0]), __ldg(&v.mm->j0[1]),
                                       __ldg(&v.mm->j0[2]), __ldg(&v.mm->j0[3]));
-    tile_body<NR, MODE_GCM, false>(smem, v, c, rk, L, tile, gc);
+    tile_body<NR>(smem, v, c, rk, L, tile, gc);
 }
 
 // The CTA that finishes a message's last tile combines its partials (the
