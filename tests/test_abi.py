@@ -64,6 +64,17 @@ def test_errors_without_a_device_are_reported_not_raised(native):
     assert "NULL" in native.last_error()
 
 
+def test_host_alloc_argument_errors(native):
+    # gcm_host_alloc checks its arguments before any CUDA call.
+    import ctypes
+
+    out = ctypes.c_void_p(1)
+    assert native.lib.gcm_host_alloc(0, 0, ctypes.byref(out)) == native.GCM_ERR_INVALID_ARG
+    assert out.value is None
+    assert native.lib.gcm_host_alloc(0, 16, None) == native.GCM_ERR_INVALID_ARG
+    assert native.lib.gcm_host_free(None) == native.GCM_OK
+
+
 def build_c_consumer(out_dir):
     """Compiles tests/abi_consumer.c (C99, warnings as errors) against the
     header and links it to the library; returns the executable's path."""
