@@ -17,6 +17,10 @@ may import it.  The product path never imports it; the two share no code.
       data unit zero-padded to whole 2880-byte records and encrypted).
     - ``paper_aad_data``: the paper's structural-keyword AAD
       (Sec. 3.2.3, the AAD_Data formula).
+* ``mapreduce.py`` -- GCM of multi-GiB messages on many host cores: the same
+  C functions applied chunk by chunk (GCTR from each chunk's counter, serial
+  GHASH per chunk), the partials joined with ``combine``; it returns the
+  tag and SHA-256 digests of the ciphertext chunks.
 """
 from __future__ import annotations
 
@@ -268,6 +272,31 @@ def gcm_decrypt(key: bytes, iv: bytes, aad: bytes, ct: bytes, tag: bytes) -> Tup
     return rc == 0, pb.raw[: len(ct)]
 
 
+def counter_block(j0: bytes, i: int) -> bytes:
+    """inc_32^i(J0): the rightmost 32 bits of J0, read big-endian, plus i
+    modulo 2^32; the leftmost 96 bits unchanged (SP 800-38D sec. 6.2 applied
+    i times).  Block j (0-based) of a payload is XORed with
+    CIPH_K(counter_block(J0, j + 1))."""
+    lo = (int.from_bytes(j0[12:16], "big") + i) & 0xFFFFFFFF
+    return bytes(j0[:12]) + lo.to_bytes(4, "big")
+
+
+def gctr_ptr(key: bytes, icb: bytes, src: int, n: int, dst: int) -> None:
+    """GCTR_K(ICB, X) (Algorithm 3) from ``n`` bytes at address ``src`` into
+    ``dst`` (host addresses, e.g. numpy ``.ctypes.data``)."""
+    w, nr = key_expansion(key)
+    wb, ib = _buf(w), _buf(icb)
+    lib().oracle_gctr(_ptr(wb), nr, _ptr(ib), src, n, dst)
+
+
+def ghash_ptr(h: bytes, src: int, nblocks: int) -> bytes:
+    """Serial GHASH_H (Algorithm 2) over ``nblocks`` whole blocks at host
+    address ``src``."""
+    hb, ob = _buf(h), ctypes.create_string_buffer(16)
+    lib().oracle_ghash(_ptr(hb), src, nblocks, _ptr(ob))
+    return ob.raw
+
+
 def gcm_encrypt_numpy(key: bytes, iv: bytes, aad: bytes, pt_array) -> Tuple["object", bytes]:
     """Oracle encryption of a numpy uint8 array without extra copies."""
     import numpy as np
@@ -309,6 +338,11 @@ def datasum(data: bytes) -> int:
     end-around carry (C oracle, word by word)."""
     b = _buf(bytes(data))
     return int(lib().oracle_datasum(_ptr(b), len(data)))
+
+
+def datasum_ptr(src: int, n: int) -> int:
+    """``datasum`` of ``n`` bytes at host address ``src``."""
+    return int(lib().oracle_datasum(src, n))
 
 
 def fits_split(fits: bytes) -> Tuple[bytes, bytes, int]:
