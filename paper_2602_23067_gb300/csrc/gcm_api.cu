@@ -111,6 +111,21 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// The ticket word of `s` for fused launches that finish their message, or
+// null when every slot is taken (the call then uses the combine kernel).
+uint32_t *ticket_for(gcm_ctx *ctx, cudaStream_t s)
+{
+    if (!ctx->tickets) return nullptr;
+    const std::thread::id who = (s == cudaStreamPerThread) ? std::this_thread::get_id() : std::thread::id();
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->ticket_slot.find({s, who});
+    if (it != ctx->ticket_slot.end()) return ctx->tickets + it->second;
+    const int n = (int)ctx->ticket_slot.size();
+    if (n >= gcm_ctx::TICKET_SLOTS) return nullptr;
+    ctx->ticket_slot.emplace(std::make_pair(s, who), n);
+    return ctx->tickets + n;
+}
+
 int scratch_alloc(gcm_ctx *ctx, size_t bytes, cudaStream_t s, Scratch &out)
 {
     {
@@ -168,9 +183,10 @@ int check_common(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8_t
 // cannot be cached now (cache disabled or every entry in use); the caller
 // then sets up private key material.  A held slot is released, after the
 // call's last kernel that reads it, by key_cache_release.
-int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &err)
+int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &err, int &launched)
 {
     err = cudaSuccess;
+    launched = 0;
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->key_cache_cap == 0) return -1;
     auto &C = ctx->key_cache;
@@ -219,6 +235,7 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
         memcpy(e.key, ks.key, ks.key_len);
         e.key_len = ks.key_len;
         err = launch_key_setup(ks, s);
+        launched = 1;
         if (err == cudaSuccess) err = cudaEventRecord(e.ready, s);
         if (err != cudaSuccess) {
             memset(e.key, 0, sizeof(e.key));
@@ -229,7 +246,10 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
         // With a 96-bit IV the caller forms J0 on the host and the combine
         // kernel derives E_K(J0), so nothing per message is needed here.
         err = cudaStreamWaitEvent(s, e.ready, 0);
-        if (err == cudaSuccess && ks.iv_len != 12) err = launch_msg_only(ks, s);
+        if (err == cudaSuccess && ks.iv_len != 12) {
+            err = launch_msg_only(ks, s);
+            launched = 1;
+        }
         if (err != cudaSuccess) return -1;
     }
     e.tick = ++ctx->key_cache_tick;
@@ -301,7 +321,8 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     ks.mm = mm;
     ks.tabs = ctx->tabs;
     cudaError_t e = cudaSuccess;
-    const int slot = key_cache_acquire(ctx, ks, s, e);
+    int setup_launches = 0;
+    const int slot = key_cache_acquire(ctx, ks, s, e, setup_launches);
     if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
     if (slot >= 0) {
         km = ks.km;
@@ -309,8 +330,9 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         ks.km = km;
         e = launch_key_setup(ks, s);
         if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
+        setup_launches = 1;
     }
-    ctx->launches += 1;
+    ctx->launches += setup_launches;
     // Releases the cache slot after the last kernel of this call that reads
     // the key material has been enqueued (on every return path below).
     struct SlotGuard {
@@ -352,6 +374,19 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
                        ((uint32_t)iv[4 * i + 3] << 24);
         kf.j0[3] = 0x01000000u;
     }
+    // Messages of a few tiles are finished by the fused launch itself (its
+    // last CTA runs the tree, the tag and the verify gate): no combine or
+    // zero-fill launch follows.
+    const bool can_finish = (mode == 2) || (mode != 1 && ctx->aes_impl == 0);
+    if (can_finish && K >= 1 && K <= FINISH_MAX_TILES && M <= FINISH_MAX_BLOCKS) {
+        kf.ticket = ticket_for(ctx, s);
+        if (kf.ticket) {
+            kf.tag_out = decrypt ? nullptr : tag_dev;
+            kf.tag_expected = decrypt ? tag_dev : nullptr;
+            kf.status = status_dev;
+            if (mode == 3) kf.datasum_out = datasum_dev;
+        }
+    }
     const int grid = (int)((K < (uint64_t)ctx->num_sms) ? K : (uint64_t)ctx->num_sms);
     const bool prof = ctx->profiling.load() != 0 && K > 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -371,6 +406,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     }
     ctx->launches += (K > 0) ? 1 : 0;
     if (mode == 1) return GCM_OK;  // CTR only: no authenticator
+    if (kf.ticket) return GCM_OK;  // finished by the fused launch
 
     KcParams kc;
     memset(&kc, 0, sizeof(kc));
@@ -639,6 +675,8 @@ int gcm_ctx_create(gcm_ctx **out, int device, size_t hbm_budget_bytes)
         if (major == 10 && minor == 3 && ctx->num_sms == 152) memcpy(ctx->tuned_lg, kTunedGB300, sizeof(kTunedGB300));
     }
     if (e == cudaSuccess) e = cudaMalloc(&ctx->tabs, sizeof(DevTables));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->tickets, gcm_ctx::TICKET_SLOTS * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMemset(ctx->tickets, 0, gcm_ctx::TICKET_SLOTS * sizeof(uint32_t));
     if (e == cudaSuccess) e = launch_build_tables(ctx->tabs, nullptr);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
@@ -802,6 +840,7 @@ void gcm_ctx_destroy(gcm_ctx *ctx)
         }
         ctx->key_cache.clear();
         if (ctx->tabs) cudaFree(ctx->tabs);
+        if (ctx->tickets) cudaFree(ctx->tickets);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;

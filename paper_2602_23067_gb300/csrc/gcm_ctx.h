@@ -4,7 +4,10 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <mutex>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -84,6 +87,14 @@ struct gcm_ctx {
     uint8_t tuned_lg[64] = {};
     // AES engine of the single-message fused pass (GCM_AES_TABLES / _BITSLICED).
     int aes_impl = 0;
+    // Ticket words of fused launches that finish their own message (the
+    // last CTA runs the combine and the tag): one zero word per stream the
+    // calls use, so that only launches ordered on one stream share a word; a
+    // launch leaves its word at zero.  The per-thread default stream is one
+    // handle for many streams, so its words are per calling thread too.
+    static constexpr int TICKET_SLOTS = 4096;
+    uint32_t *tickets = nullptr;
+    std::map<std::pair<cudaStream_t, std::thread::id>, int> ticket_slot;  // guarded by mu
 };
 
 namespace gcmgpu {

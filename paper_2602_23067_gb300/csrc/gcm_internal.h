@@ -100,7 +100,20 @@ struct KfParams {
     uint32_t j0_given;      // 1: J0 is j0 below (96-bit IV, formed on the host), else mm->j0
     uint32_t j0[4];         // memory words
     uint32_t *dsums;        // K per-tile DATASUM partials (mode 3 only)
+    // Finishing in the same launch (1 <= K <= FINISH_MAX_TILES, M <=
+    // FINISH_MAX_BLOCKS; modes 0, 2, 3): the last CTA to finish runs the
+    // combine, the length block, the tag and the verify gate.  ticket is a
+    // zero word that only launches on one stream share (left at zero).
+    uint32_t *ticket;       // null: a separate combine kernel follows
+    uint8_t *tag_out;       // 16 bytes (device): the tag, or GHASH_H(A, C) in mode 2
+    const uint8_t *tag_expected;  // 16 bytes (device) for decryption, else null
+    int32_t *status;        // device verdict word (decryption), may be null
+    uint32_t *datasum_out;  // mode 3: the message's DATASUM
 };
+// Largest message finished by the fused launch itself: the tile partials fit
+// in shared memory and a failed tag's zero-fill by one CTA stays short.
+constexpr uint64_t FINISH_MAX_TILES = 1024;
+constexpr uint64_t FINISH_MAX_BLOCKS = 1ull << 22;  // 64 MiB of payload + AAD
 
 // One message of a device-memory batch (gcm_batch with GCM_MEM_DEVICE).
 struct BatchMsg {

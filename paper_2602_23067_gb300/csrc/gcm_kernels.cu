@@ -712,6 +712,156 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     __syncthreads();
 }
 
+// E_K(J0) through the replicated round tables in shared memory (every lane
+// of the calling warp computes the same block; each reads its own bank).
+// rk holds round-key words 12 .. 4 NR + 3.
+template <int NR>
+__device__ __forceinline__ uint4 aes_block_smem(const uint8_t *smem, const LaneConst &L, const KeyMat *km,
+                                                const uint32_t *rk, const uint32_t j0[4])
+{
+    const uint8_t *t01 = smem + SM_T01;
+    const uint8_t *t23 = smem + SM_T23;
+    uint32_t s0 = j0[0] ^ __ldg(&km->rk[0]), s1 = j0[1] ^ __ldg(&km->rk[1]);
+    uint32_t s2 = j0[2] ^ __ldg(&km->rk[2]), s3 = j0[3] ^ __ldg(&km->rk[3]);
+    aes_round(t01, t23, L, s0, s1, s2, s3, __ldg(&km->rk[4]), __ldg(&km->rk[5]), __ldg(&km->rk[6]),
+              __ldg(&km->rk[7]));
+    aes_round(t01, t23, L, s0, s1, s2, s3, __ldg(&km->rk[8]), __ldg(&km->rk[9]), __ldg(&km->rk[10]),
+              __ldg(&km->rk[11]));
+    return aes_rounds_from3<NR>(t01, t23, L, s0, s1, s2, s3, rk);
+}
+
+// The reduce phase of a message with few tiles, run by the last CTA of the
+// fused launch to finish (Sec. 5.2.2; the same tree, length block, tag and
+// verify gate as the separate combine kernel, without its launch):
+//   * warp 0 computes E_K(J0) from the round tables still in shared memory;
+//   * the K <= FINISH_MAX_TILES tile partials (written by every CTA before
+//     its ticket) are staged into shared memory over the round tables, and
+//     reduced level by level with Combine(L, R) = L * H^(2^(lg + level)) xor
+//     R, R read from the end of the sequence (the tiles are end-aligned, so
+//     every right operand is a full group of 2^level tiles);
+//   * GHASH = (P xor [len A]_64 || [len C]_64) * H, T = E_K(J0) xor GHASH;
+//     decryption compares T with the expected tag in constant time and, on a
+//     mismatch, zero-fills the whole payload before the kernel ends.
+// Kept out of line so that it does not take registers from the tile loop.
+template <int NR, int MODE>
+__device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
+{
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+    const KeyMat *km = p.km;
+    uint32_t *sej0 = reinterpret_cast<uint32_t *>(smem + SM_RED);
+    int32_t *sfail = reinterpret_cast<int32_t *>(smem + SM_RED + 16);
+    if (warp == 0) {
+        uint4 e = make_uint4(0u, 0u, 0u, 0u);
+        if (MODE != MODE_GHASH) {
+            if (p.j0_given) {
+                uint32_t rk[4 * (NR + 1)];
+#pragma unroll
+                for (int i = 12; i < 4 * (NR + 1); i++) rk[i] = __ldg(&km->rk[i]);
+                e = aes_block_smem<NR>(smem, make_lane_const(lane), km, rk, p.j0);
+            } else {
+                e.x = __ldg(&p.mm->ej0[0]);
+                e.y = __ldg(&p.mm->ej0[1]);
+                e.z = __ldg(&p.mm->ej0[2]);
+                e.w = __ldg(&p.mm->ej0[3]);
+            }
+        }
+        if (lane == 0) {
+            sej0[0] = e.x; sej0[1] = e.y; sej0[2] = e.z; sej0[3] = e.w;
+            *sfail = 0;
+        }
+    }
+    __syncthreads();  // the round tables are no longer read below
+    gf128 *sbuf0 = reinterpret_cast<gf128 *>(smem);
+    gf128 *sbuf1 = reinterpret_cast<gf128 *>(smem + 16 * FINISH_MAX_TILES);
+    gf128 *smult = reinterpret_cast<gf128 *>(smem + 32 * FINISH_MAX_TILES);
+    uint64_t *wscr = reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp;
+    const uint64_t K = p.K;
+    for (uint64_t i = t; i < K; i += blockDim.x)
+        for (int k = 0; k < 4; k++) sbuf1[i].w[k] = __ldcg(&p.partials[i].w[k]);
+    if (t < H2K_COUNT && (uint32_t)t + p.tile_log2 < (uint32_t)H2K_COUNT) smult[t] = km->h2k[p.tile_log2 + t];
+    if (t == H2K_COUNT) smult[H2K_COUNT] = km->H;
+    __syncthreads();
+    uint64_t cnt = K;
+    int level = 0;
+    const gf128 *src = sbuf1;
+    bool reversed = true;
+    gf128 *dst = sbuf0;
+    while (cnt > 1) {
+        const uint64_t half = (cnt + 1) / 2;
+        const gf128 mult = smult[level];
+        if (half > (uint64_t)nwarps * 4) {
+            for (uint64_t g = t; g < half; g += blockDim.x) {
+                const uint64_t ri = 2 * g, li = 2 * g + 1;
+                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
+                if (li < cnt) v = gf_xor(gf_mul(reversed ? src[cnt - 1 - li] : src[li], mult), v);
+                dst[g] = v;
+            }
+        } else {
+            for (uint64_t g = warp; g < half; g += nwarps) {
+                const uint64_t ri = 2 * g, li = 2 * g + 1;
+                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
+                if (li < cnt) v = gf_xor(gf_mul_warp(reversed ? src[cnt - 1 - li] : src[li], mult, wscr), v);
+                if (lane == 0) dst[g] = v;
+            }
+        }
+        __syncthreads();
+        const gf128 *done = dst;
+        dst = (dst == sbuf0) ? sbuf1 : sbuf0;
+        src = done;
+        reversed = false;
+        cnt = half;
+        level++;
+    }
+    if (MODE == MODE_GCM_SUM) {
+        uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
+        uint64_t acc = 0;
+        for (uint64_t i = t; i < K; i += blockDim.x) acc += __ldcg(&p.dsums[i]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+        if (lane == 0) dred[warp] = acc;
+        __syncthreads();
+        if (t == 0) {
+            uint64_t tot = 0;
+            for (int w = 0; w < nwarps; w++) tot += dred[w];
+            *p.datasum_out = ones_fold(tot);
+        }
+    }
+    if (warp == 0) {
+        const gf128 s = src[0];
+        gf128 lb;
+        const uint64_t abits = p.aad_len * 8u, cbits = p.len * 8u;
+        lb.w[0] = (uint32_t)(abits >> 32);
+        lb.w[1] = (uint32_t)abits;
+        lb.w[2] = (uint32_t)(cbits >> 32);
+        lb.w[3] = (uint32_t)cbits;
+        const gf128 gh = gf_mul_warp(gf_xor(s, lb), smult[H2K_COUNT], wscr);
+        if (lane == 0) {
+            const uint4 gm = gf_to_mem(gh);
+            const uint32_t tw[4] = {gm.x ^ sej0[0], gm.y ^ sej0[1], gm.z ^ sej0[2], gm.w ^ sej0[3]};
+            if (p.tag_out)
+                for (int b = 0; b < 16; b++) p.tag_out[b] = (uint8_t)(tw[b >> 2] >> (8 * (b & 3)));
+            if (p.tag_expected) {
+                uint32_t diff = 0;
+                for (int b = 0; b < 16; b++)
+                    diff |= (uint32_t)((uint8_t)(tw[b >> 2] >> (8 * (b & 3))) ^ p.tag_expected[b]);
+                if (p.status) *p.status = diff ? -3 : 0;
+                *sfail = diff ? 1 : 0;
+            } else if (p.status) {
+                *p.status = 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (*sfail) {
+        // Payload suppression: the whole output is zeroed before the kernel
+        // ends (messages on this path hold at most FINISH_MAX_BLOCKS blocks).
+        const uint64_t nvec = p.len / 16;
+        uint4 *o = reinterpret_cast<uint4 *>(p.out);
+        for (uint64_t i = t; i < nvec; i += blockDim.x) o[i] = make_uint4(0u, 0u, 0u, 0u);
+        if (t < (int)(p.len & 15)) p.out[nvec * 16 + t] = 0;
+    }
+}
+
 // KF: one message, tiles [tile_begin, tile_end) over a persistent grid.
 template <int NR, int MODE = MODE_GCM>
 __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_constant__ KfParams p)
@@ -752,6 +902,22 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
     gc.P0 = gc.P1 = gc.P2 = gc.P3 = 0u;
     for (uint64_t tile = p.tile_begin + blockIdx.x; tile < p.tile_end; tile += gridDim.x)
         tile_body<NR, MODE>(smem, v, c, rk, L, tile, gc);
+    if (MODE != MODE_CTR && p.ticket) {
+        // Thread 0 wrote this CTA's partials (tile_body ends with a barrier);
+        // make them visible device-wide, then take a ticket.  atomicInc wraps
+        // the counter back to 0 on the last ticket, so the word is ready for
+        // the next launch on the same stream.
+        __shared__ int s_last;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = (atomicInc(p.ticket, gridDim.x - 1) == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            __threadfence();
+            finish_message<NR, MODE>(smem, p);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------
