@@ -4,13 +4,16 @@ the benchmark times: one gcm_batch call over the 10,000-message mix
 multiples of 16, AES-128/AES-256 with distinct keys, 5% IVs of 8..128
 bytes, AAD 0..4 KiB; 33.8 GB of payload in device memory).
 
-The oracle cannot encrypt 33.8 GB in test time, so the checks are ones it
-can make message by message or block by block, or that hold at any size:
+The oracle cannot encrypt all 33.8 GB in test time, so it checks whole
+messages chosen across the length range, and single blocks:
   * the first 120 messages of at most 256 KiB: ciphertext and tag equal the
     oracle's, byte for byte;
-  * the 12 longest messages: sampled blocks (both ends, tile edges, random)
-    equal P_j xor E_K(inc32^(j+1)(J0)) from the oracle's keystream, and the
-    tag equals that of gcm_encrypt of the same message alone;
+  * the 12 longest messages (up to 64 MiB, many tiles each) and 36 random
+    messages above 256 KiB, whole: ciphertext (SHA-256 of 8 MiB chunks) and
+    tag equal those of the oracle run chunk by chunk on all host cores
+    (``oracle.mapreduce``);
+  * sampled blocks of the 12 longest (both ends, tile edges, random) equal
+    P_j xor E_K(inc32^(j+1)(J0)) from single oracle keystream blocks;
   * decrypt-verify of the whole batch, in place, accepts every message and
     gives back every plaintext.
 """
@@ -21,6 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mapreduce
 from paper_2602_23067_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -97,9 +101,31 @@ def test_ten_thousand_messages_in_one_launch():
             assert host(arena_out, i, lens[i]) == ref_ct, i
             assert bytes(host_tags[i]) == ref_tag, i
 
-        # long messages: sampled blocks against the oracle's keystream, tag alone vs in the mix
+        # the 12 longest messages and 36 random ones of 256 KiB..64 MiB, whole:
+        # ciphertext digests and tags against the chunked oracle on all host
+        # cores (GCTR from each chunk's counter, serial GHASH per chunk,
+        # partials joined by Combine, length block, E_K(J0))
         longest = sorted(range(COUNT), key=lambda i: -lens[i])[:12]
         r = random.Random(34)
+        mid = [i for i in range(COUNT) if (256 << 10) < lens[i] and i not in longest]
+        whole = longest + r.sample(mid, 36)
+        total_whole = sum(lens[i] for i in whole)
+        chunk = 8 << 20
+        with mapreduce.HostInput(total_whole) as src:
+            spec, o = [], 0
+            for i in whole:
+                torch.from_numpy(src.array[o:o + lens[i]]).copy_(arena_in[int(offs[i]): int(offs[i]) + lens[i]])
+                spec.append({"key": descs[i]["key"], "iv": descs[i]["iv"], "aad": aad_of(i), "off": o,
+                             "len": lens[i]})
+                o += lens[i]
+            ref = mapreduce.gcm_encrypt_digests(spec, src, chunk_bytes=chunk)
+        for i, (ref_dg, ref_tag) in zip(whole, ref):
+            assert bytes(host_tags[i]) == ref_tag, i
+            got = arena_out[int(offs[i]): int(offs[i]) + lens[i]].cpu().numpy()
+            assert mapreduce.digests(got, chunk) == ref_dg, i
+
+        # sampled blocks of the longest messages against single oracle
+        # keystream blocks (both ends, tile edges, random)
         for i in longest:
             d = descs[i]
             n = lens[i]
@@ -122,13 +148,6 @@ def test_ten_thousand_messages_in_one_launch():
                 c = bytes(arena_out[base + 16 * j: base + 16 * j + w].cpu().numpy())
                 ks = oracle.keystream_block(d["key"], j0, j + 1)[:w]
                 assert c == bytes(x ^ y for x, y in zip(p, ks)), (i, j)
-            alone_ct = torch.empty(n, dtype=torch.uint8, device="cuda")
-            aad_dev = aad_arena[int(aoffs[i]): int(aoffs[i]) + aad_sizes[i]] if aad_sizes[i] else None
-            _, alone_tag = ctx.encrypt_device(d["key"], d["iv"], aad_dev, arena_in[base: base + n], ct=alone_ct)
-            torch.cuda.synchronize()
-            assert bytes(alone_tag.cpu().numpy()) == bytes(host_tags[i]), i
-            assert torch.equal(alone_ct, arena_out[base: base + n]), i
-            del alone_ct
 
         # the whole batch back, in place
         rc = _native.lib.gcm_batch(ctx.handle, msgs(arena_out, arena_out), COUNT, 1, status, 0, stream.cuda_stream)

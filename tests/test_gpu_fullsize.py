@@ -1,17 +1,22 @@
 """Full-size parity for the single large message (AES-256, a 32768 x 32768
 float32 FITS image: 4,294,969,920 bytes of record-padded data unit behind a
-2880-byte header used as AAD), in the same launch configuration the
-benchmark times.
+2880-byte header used as AAD), through the call and launch configuration the
+benchmark times (gfc_fits_encrypt / gfc_fits_decrypt_verify on the device
+FITS file), and through the plain gcm_encrypt.
 
-The oracle cannot run 4 GiB in test time, so the checks are ones it can make
-one item at a time or that hold at any size:
-  * sampled ciphertext blocks equal P_j xor E_K(inc32^j(J0)), block by block;
-  * decrypt-verify of the ciphertext returns the plaintext;
-  * GHASH is linear in C: for a ciphertext that is zero except at chosen
-    blocks, the tag has a closed form the oracle evaluates with a few powers
-    of H (so the tree combine, tile placement and length block are checked
-    at full scale), and changing chosen blocks of the real ciphertext
-    changes its tag by the same closed form.
+* The whole ciphertext and the tag against the oracle: the oracle's own
+  definitions run chunk by chunk on all host cores (``oracle.mapreduce``:
+  GCTR from each chunk's counter, serial GHASH per chunk, partials joined by
+  Combine, the length block and E_K(J0)); the ciphertexts are compared by
+  the SHA-256 digests of their 64 MiB chunks, the tags byte for byte.
+* The DATASUM computed in the cipher pass against the oracle's DATASUM of
+  that (oracle-equal) ciphertext.
+* Sampled ciphertext blocks against single oracle keystream blocks (tile
+  edges at several tile sizes, both ends, random blocks).
+* decrypt-verify of the ciphertext gives back the file; a sparse ciphertext
+  whose tag the oracle evaluates in closed form (a few powers of H) is
+  accepted, and a one-bit change of that tag is rejected with the output
+  zero-filled.
 """
 import random
 
@@ -19,6 +24,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import mapreduce
 from paper_2602_23067_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -26,6 +32,7 @@ pytestmark = pytest.mark.gpu
 N1 = N2 = 32768
 DATA_BYTES = N1 * N2 * 4
 PADDED = workloads.padded_len(DATA_BYTES)
+CHUNK = 64 << 20
 
 
 @pytest.fixture(scope="module")
@@ -40,16 +47,71 @@ def setup():
     key = r.integers(0, 256, 32, dtype=np.uint8).tobytes()
     iv = r.integers(0, 256, 12, dtype=np.uint8).tobytes()
     header = workloads.fits_header(2, -32, [N1, N2], ncards=36)
-    assert len(header) == 2880 and PADDED == 4294969920
-    pt = torch.empty(PADDED, dtype=torch.uint8, device="cuda")
-    workloads.sky_image_device(2, N1, N2, out=pt)
-    aad = torch.frombuffer(bytearray(header), dtype=torch.uint8).cuda()
-    ct, tag = ctx.encrypt_device(key, iv, aad, pt)
+    hl = len(header)
+    assert hl == 2880 and PADDED == 4294969920
+    # the benchmark's FITS file: header records, then the padded data unit
+    fits = torch.empty(hl + PADDED, dtype=torch.uint8, device="cuda")
+    fits[:hl].copy_(torch.frombuffer(bytearray(header), dtype=torch.uint8))
+    workloads.sky_image_device(2, N1, N2, out=fits[hl:])
+    pt = fits[hl:]
+    stream = torch.cuda.current_stream()
+    enc, tag = ctx.fits_encrypt_raw(key, fits, iv, stream=stream)
     torch.cuda.synchronize()
-    yield torch, ctx, key, iv, header, aad, pt, ct, bytes(tag.cpu().numpy().tobytes())
-    del pt, ct
+    enc_file = Context.result_view(enc)
+    assert enc_file.numel() == hl + PADDED
+    aad = fits[:hl]
+    ct_plain, tag_plain = ctx.encrypt_device(key, iv, aad, pt)
+    torch.cuda.synchronize()
+    yield {"torch": torch, "ctx": ctx, "key": key, "iv": iv, "header": header, "aad": aad, "fits": fits, "pt": pt,
+           "enc": enc, "enc_file": enc_file, "ct": enc_file[hl:], "tag": tag, "datasum": int(enc.datasum),
+           "datasum_valid": bool(enc.datasum_valid), "ct_plain": ct_plain,
+           "tag_plain": bytes(tag_plain.cpu().numpy().tobytes())}
+    ctx.release(enc)
+    del fits, pt, ct_plain
     ctx.close()
     torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def oracle_ref(setup):
+    """Digests and tag of the whole message from the chunked oracle."""
+    torch = setup["torch"]
+    with mapreduce.HostInput(PADDED) as src:
+        torch.from_numpy(src.array).copy_(setup["pt"])
+        (dg, tag), = mapreduce.gcm_encrypt_digests(
+            [{"key": setup["key"], "iv": setup["iv"], "aad": setup["header"], "off": 0, "len": PADDED}], src,
+            chunk_bytes=CHUNK)
+    return dg, tag
+
+
+def host_digests(torch, t):
+    host = torch.empty(t.numel(), dtype=torch.uint8)
+    host.copy_(t)
+    return mapreduce.digests(host.numpy(), CHUNK), host
+
+
+def test_fits_call_whole_ciphertext_and_tag_against_the_oracle(setup, oracle_ref):
+    torch = setup["torch"]
+    ref_dg, ref_tag = oracle_ref
+    assert len(ref_dg) == (PADDED + CHUNK - 1) // CHUNK
+    assert setup["tag"] == ref_tag
+    assert torch.equal(setup["enc_file"][:2880], setup["fits"][:2880])  # header stays in clear
+    dg, host = host_digests(torch, setup["ct"])
+    bad = [i for i, (a, b) in enumerate(zip(dg, ref_dg)) if a != b]
+    assert not bad, "ciphertext chunks differing from the oracle: %s" % bad[:10]
+    # DATASUM of the encrypted data unit, from the same pass
+    assert setup["datasum_valid"]
+    assert setup["datasum"] == oracle.datasum_ptr(host.data_ptr(), PADDED)
+    del host
+
+
+def test_plain_call_whole_ciphertext_and_tag_against_the_oracle(setup, oracle_ref):
+    torch = setup["torch"]
+    ref_dg, ref_tag = oracle_ref
+    assert setup["tag_plain"] == ref_tag
+    dg, host = host_digests(torch, setup["ct_plain"])
+    assert dg == ref_dg
+    del host
 
 
 def blocks_at(torch, t, idx):
@@ -72,25 +134,28 @@ def sample_indices(nblocks, seed, k=1500):
 
 
 def test_sampled_ciphertext_blocks(setup):
-    torch, ctx, key, iv, header, aad, pt, ct, tag = setup
+    torch = setup["torch"]
     n = PADDED // 16
     idx = sample_indices(n, 1)
-    p = blocks_at(torch, pt, idx)
-    c = blocks_at(torch, ct, idx)
-    _, j0, _ = oracle.h_j0(key, iv)
+    p = blocks_at(torch, setup["pt"], idx)
+    c = blocks_at(torch, setup["ct"], idx)
+    _, j0, _ = oracle.h_j0(setup["key"], setup["iv"])
     for k, j in enumerate(idx):
-        ks = np.frombuffer(oracle.keystream_block(key, j0, j + 1), dtype=np.uint8)
+        ks = np.frombuffer(oracle.keystream_block(setup["key"], j0, j + 1), dtype=np.uint8)
         assert np.array_equal(c[k], p[k] ^ ks), j
 
 
-def test_roundtrip(setup):
-    torch, ctx, key, iv, header, aad, pt, ct, tag = setup
-    t = torch.frombuffer(bytearray(tag), dtype=torch.uint8).cuda()
-    out = torch.empty_like(ct)
-    ctx.decrypt_verify_device(key, iv, aad, ct, t, pt=out)
+def test_roundtrip_through_the_fits_call(setup):
+    torch, ctx = setup["torch"], setup["ctx"]
+    from paper_2602_23067_gb300 import Context
+
+    enc = setup["enc"]
+    dec = ctx.fits_decrypt_verify_raw(setup["key"], enc.data_buffer, enc.buffer_size, setup["iv"], setup["tag"],
+                                      stream=torch.cuda.current_stream())
     torch.cuda.synchronize()
-    assert torch.equal(out, pt)
-    del out
+    assert dec.error_code == 0
+    assert torch.equal(Context.result_view(dec), setup["fits"])
+    ctx.release(dec)
 
 
 def _ghash_terms(h, blocks, positions, n):
@@ -102,7 +167,8 @@ def _ghash_terms(h, blocks, positions, n):
 
 
 def test_sparse_ciphertext_closed_form_tag(setup):
-    torch, ctx, key, iv, header, aad, pt, ct, tag = setup
+    torch, ctx = setup["torch"], setup["ctx"]
+    key, iv, header, aad = setup["key"], setup["iv"], setup["header"], setup["aad"]
     from paper_2602_23067_gb300 import GcmError
 
     n = PADDED // 16
@@ -138,22 +204,3 @@ def test_sparse_ciphertext_closed_form_tag(setup):
     torch.cuda.synchronize()
     assert int(out.view(torch.int64).abs().sum().item()) == 0
     del sparse, out
-
-
-def test_tag_shift_under_sparse_edits(setup):
-    torch, ctx, key, iv, header, aad, pt, ct, tag = setup
-    n = PADDED // 16
-    h, _, _ = oracle.h_j0(key, iv)
-    r = random.Random(5)
-    idx = sample_indices(n, 6, k=64)
-    deltas = [bytes(r.getrandbits(8) for _ in range(16)) for _ in idx]
-    edited = ct.clone()
-    ii = torch.tensor(idx, dtype=torch.int64, device="cuda")
-    d = torch.tensor(np.frombuffer(b"".join(deltas), dtype=np.uint8).reshape(-1, 16), device="cuda")
-    edited.view(-1, 16).index_copy_(0, ii, edited.view(-1, 16).index_select(0, ii) ^ d)
-    new_tag = oracle.xor16(tag, _ghash_terms(h, deltas, [j + 1 for j in idx], n))
-    t = torch.frombuffer(bytearray(new_tag), dtype=torch.uint8).cuda()
-    out = torch.empty_like(edited)
-    ctx.decrypt_verify_device(key, iv, aad, edited, t, pt=out)
-    torch.cuda.synchronize()
-    del edited, out
