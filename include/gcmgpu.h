@@ -362,6 +362,15 @@ size_t gcm_server_poll(gcm_server *srv, gcm_completion *out, size_t max);
 int gcm_server_stats(gcm_server *srv, uint64_t *waves, uint64_t *messages, size_t *queued,
                      size_t *bytes_in_flight);
 
+/* Admission under the HBM budget (spec serving: requests are admitted
+ * as memory frees up): the budget in force, the largest number of device
+ * bytes that waves in flight held at once (never above the budget), and
+ * how many requests were held back at least once because the next wave
+ * would have exceeded the budget.  Any pointer may be NULL.  Returns 0, or
+ * GCM_ERR_INVALID_ARG for a NULL server. */
+int gcm_server_admission(gcm_server *srv, size_t *budget, size_t *peak_bytes_in_flight,
+                         uint64_t *budget_waits);
+
 /* Time spent so far, summed over waves (ms): out[0] host time issuing
  * waves, out[1] copy-in stage, out[2] compute stage (from copy-in done to
  * kernels done, queueing included), out[3] copy-out stage. */
@@ -556,7 +565,10 @@ void gfc_result_free(gcm_ctx *ctx, gfc_result *res);
  * The first call on each device sets that device up (finds the array's
  * device address, builds the round tables in it) and synchronises `stream`;
  * make that first call before any stream capture.  Later calls only enqueue
- * work on `stream` and return.
+ * work on `stream` and return.  The set-up belongs to the CUDA context it
+ * was made in: after a device reset (or under another context) the next
+ * call detects the new context and sets up again, synchronising as the
+ * first call does.
  *
  * Every call shares the one array and the array keeps the last call's
  * contents, so calls whose work overlaps on the GPU (e.g. issued on two

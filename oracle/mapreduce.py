@@ -95,14 +95,20 @@ class HostInput:
 
 
 def _chunk_job(args) -> Tuple[bytes, bytes]:
-    """Worker: ciphertext digest and GHASH partial of one payload chunk."""
-    path, total, off, n, key, icb, h = args
+    """Worker: ciphertext digest and GHASH partial of one payload chunk (and
+    the chunk's ciphertext written to the output file, when one is given)."""
+    path, total, off, n, key, icb, h, dest = args
     src = np.memmap(path, dtype=np.uint8, mode="r", shape=(total,))[off: off + n]
     src = np.ascontiguousarray(src)  # one read of the chunk into this process
     ct = np.empty(n + (-n) % 16, dtype=np.uint8)
     ct[n:] = 0  # zero pad of a final partial block (GHASH input only)
     oracle.gctr_ptr(key, icb, src.ctypes.data, n, ct.ctypes.data)
     partial = oracle.ghash_ptr(h, ct.ctypes.data, ct.size // 16)
+    if dest is not None:
+        out = np.memmap(dest, dtype=np.uint8, mode="r+", shape=(total,))
+        out[off: off + n] = ct[:n]
+        out.flush()
+        del out
     return hashlib.sha256(ct[:n].data).digest(), partial
 
 
@@ -133,20 +139,28 @@ def _finish(key: bytes, iv: bytes, aad: bytes, length: int, parts: Sequence[Tupl
 
 
 def gcm_encrypt_digests(messages: Sequence[Dict], source: HostInput, chunk_bytes: int = 64 << 20,
-                        workers: Optional[int] = None) -> List[Tuple[List[bytes], bytes]]:
+                        workers: Optional[int] = None,
+                        dest: Optional[HostInput] = None) -> List[Tuple[List[bytes], bytes]]:
     """GCM-AE of each message, computed chunk by chunk on ``workers`` processes.
 
     Each message is a dict with ``key``, ``iv``, ``aad`` (bytes) and ``off``,
     ``len``: its plaintext is ``source.array[off:off + len]``.  Returns, per
-    message, (SHA-256 digests of its ciphertext cut by ``chunk_bounds``, tag)."""
+    message, (SHA-256 digests of its ciphertext cut by ``chunk_bounds``, tag).
+    With ``dest`` (a HostInput of the same size), the ciphertext itself is
+    also written to ``dest.array[off:off + len]``."""
     source.array.flush()
+    if dest is not None:
+        if dest.nbytes != source.nbytes:
+            raise ValueError("dest must have the size of source")
+        dest.array.flush()
     jobs: List = []
     owner: List[List[Tuple[int, int]]] = [[] for _ in messages]  # per message: (job index, blocks)
     for mi, m in enumerate(messages):
         h, j0, _ = oracle.h_j0(m["key"], m["iv"])
         for a, b in chunk_bounds(int(m["len"]), chunk_bytes):
             icb = oracle.counter_block(j0, a // 16 + 1)
-            jobs.append((source.path, max(1, source.nbytes), int(m["off"]) + a, b - a, m["key"], icb, h))
+            jobs.append((source.path, max(1, source.nbytes), int(m["off"]) + a, b - a, m["key"], icb, h,
+                         dest.path if dest is not None else None))
             owner[mi].append((len(jobs) - 1, (b - a + 15) // 16))
     results: List = [None] * len(jobs)
     if jobs:

@@ -111,6 +111,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "gcm_server_destroy": (None, [_VP]),
     "gcm_server_timing": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "gcm_server_admission": (ctypes.c_int, [_VP, ctypes.POINTER(_SZ), ctypes.POINTER(_SZ),
+                                            ctypes.POINTER(ctypes.c_uint64)]),
     "gcm_now_ns": (ctypes.c_uint64, []),
     "gcm_batch_timed": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_uint64), _VP]),

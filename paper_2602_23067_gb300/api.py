@@ -549,7 +549,10 @@ class Server:
     def stats(self):
         w, m, q, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t(), ctypes.c_size_t()
         rc = lib.gcm_server_stats(self.handle, ctypes.byref(w), ctypes.byref(m), ctypes.byref(q), ctypes.byref(b))
-        return {"waves": w.value, "messages": m.value, "queued": q.value, "bytes_in_flight": b.value, "error": rc}
+        bud, peak, waits = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_uint64()
+        check(lib.gcm_server_admission(self.handle, ctypes.byref(bud), ctypes.byref(peak), ctypes.byref(waits)))
+        return {"waves": w.value, "messages": m.value, "queued": q.value, "bytes_in_flight": b.value, "error": rc,
+                "budget": bud.value, "peak_bytes_in_flight": peak.value, "budget_waits": waits.value}
 
     def close(self) -> None:
         if self.handle:

@@ -50,6 +50,7 @@ struct Pending {
     uint64_t t_arrival;
     std::vector<uint8_t> iv;
     uint8_t tag_in[16];
+    bool waited = false;  // once held back because the HBM budget was taken
 };
 
 struct Wave {
@@ -90,6 +91,8 @@ struct gcm_server {
     std::atomic<bool> stop{false};
     std::thread worker;
     size_t bytes_in_flight = 0;
+    size_t peak_bytes_in_flight = 0;  // largest bytes_in_flight after an admission
+    uint64_t budget_waits = 0;        // requests held back at least once for memory
     std::atomic<uint64_t> waves{0}, launched_msgs{0};
     int fatal = 0;
 };
@@ -341,7 +344,16 @@ void worker_loop(gcm_server *S)
                 const size_t b = request_bytes(S, pending[n].r);
                 const size_t m = n + 1, iv2 = ivt + pending[n].iv.size();
                 const size_t sn = al(m * sizeof(BatchMsg)) + al(m * sizeof(BatchKey)) + al(iv2) + al(16 * m) + 32 * m;
-                if (wave_bytes + b > avail || sn > S->stage_bytes) break;
+                if (wave_bytes + b > avail) {
+                    // Held back until waves in flight release their memory.
+                    if (!pending[n].waited) {
+                        pending[n].waited = true;
+                        std::lock_guard<std::mutex> lk(S->mu);
+                        S->budget_waits++;
+                    }
+                    break;
+                }
+                if (sn > S->stage_bytes) break;
                 wave_bytes += b;
                 ivt = iv2;
                 n++;
@@ -357,6 +369,7 @@ void worker_loop(gcm_server *S)
             {
                 std::lock_guard<std::mutex> lk(S->mu);
                 S->bytes_in_flight += wave_bytes;
+                if (S->bytes_in_flight > S->peak_bytes_in_flight) S->peak_bytes_in_flight = S->bytes_in_flight;
                 S->slot_busy[slot] = true;
             }
             const uint64_t th0 = now_ns();
@@ -567,6 +580,16 @@ int gcm_server_stats(gcm_server *S, uint64_t *waves, uint64_t *messages, size_t 
     if (queued) *queued = S->queue.size();
     if (bytes_in_flight) *bytes_in_flight = S->bytes_in_flight;
     return S->fatal;
+}
+
+int gcm_server_admission(gcm_server *S, size_t *budget, size_t *peak_bytes_in_flight, uint64_t *budget_waits)
+{
+    if (!S) return ctx_fail(GCM_ERR_INVALID_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (budget) *budget = S->budget;
+    if (peak_bytes_in_flight) *peak_bytes_in_flight = S->peak_bytes_in_flight;
+    if (budget_waits) *budget_waits = S->budget_waits;
+    return GCM_OK;
 }
 
 int gcm_server_timing(gcm_server *S, double out[4])

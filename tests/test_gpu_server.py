@@ -129,3 +129,95 @@ def test_server_rejects_bad_requests(env):
         assert done and done[0][1] == 0
         ref_ct, ref_tag = oracle.gcm_encrypt(bytes(16), bytes(12), b"", big.tobytes())
         assert tag.tobytes() == ref_tag and out.tobytes() == ref_ct
+
+
+def test_admission_under_a_binding_budget_with_mib_requests(env):
+    # Staged host access, so that every payload occupies device memory, and a
+    # 48 MiB budget for about 150 MiB of requests queued at once (4..32 MiB
+    # and small ones, encrypt and decrypt-verify, one tampered tag): the
+    # server must hold requests back until waves in flight release memory,
+    # never hold more than the budget, and still give every request the
+    # oracle's result.  The oracle runs chunk by chunk on the host cores.
+    torch, ctx = env
+    from oracle import mapreduce
+
+    keys = [bytes(range(32)), bytes(range(16)), bytes(range(100, 124))]
+    handles = [ctx.key_register(k) for k in keys]
+    r = random.Random(71)
+    sizes = [32 << 20, 4 << 20, 2880, 16 << 20, (8 << 20) + 5, 70000, (32 << 20) - 2880, (4 << 20) + 7, 5000,
+             16 << 20, (24 << 20) + 3, 0, 200003]
+    reqs = []
+    for i, n in enumerate(sizes):
+        k = r.randrange(len(keys))
+        iv = bytes(r.getrandbits(8) for _ in range(12 if i % 4 else 40))
+        aad = bytes(r.getrandbits(8) for _ in range(r.choice((0, 20, 2880))))
+        reqs.append({"k": k, "key": keys[k], "iv": iv, "aad": aad, "n": n, "op": i % 2,
+                     "bad": i == 9})
+    total = sum(q["n"] for q in reqs)
+    with mapreduce.HostInput(total) as src, mapreduce.HostInput(total) as dst:
+        spec, off = [], 0
+        for i, q in enumerate(reqs):
+            src.array[off:off + q["n"]] = workloads.random_bytes(7100 + i, q["n"])
+            spec.append({"key": q["key"], "iv": q["iv"], "aad": q["aad"], "off": off, "len": q["n"]})
+            q["off"] = off
+            off += q["n"]
+        ref = mapreduce.gcm_encrypt_digests(spec, src, chunk_bytes=4 << 20, dest=dst)
+        pts = np.array(src.array[:max(1, total)])
+        cts = np.array(dst.array[:max(1, total)])
+    budget = 48 << 20
+    ctx.set_host_access(2)
+    try:
+        # every buffer is ready before the first submission, so the requests
+        # reach the server's queue within a fraction of the first wave's time
+        bufs = []
+        for i, q in enumerate(reqs):
+            o, n = q["off"], q["n"]
+            if q["op"] == 0:
+                inp, tag = pts[o:o + n].copy(), np.zeros(16, np.uint8)
+            else:
+                inp = cts[o:o + n].copy()
+                tb = bytearray(ref[i][1])
+                if q["bad"]:
+                    tb[7] ^= 0x40
+                tag = np.frombuffer(bytes(tb), dtype=np.uint8).copy()
+            bufs.append((inp, np.full(max(1, n), 0xA5, dtype=np.uint8), tag))
+        srv = ctx.server(hbm_budget_bytes=budget, max_wave_msgs=64, max_inflight=3)
+        try:
+            pending = {}
+            for i, q in enumerate(reqs):
+                n = q["n"]
+                inp, out, tag = bufs[i]
+                t = srv.submit(q["op"], handles[q["k"]], q["iv"], q["aad"] or None,
+                               inp if n else np.zeros(0, np.uint8), out[:n] if n else out[:0], tag, user=i)
+                pending[t] = (i, inp, out, tag)
+            done = {}
+            deadline = time.time() + 300
+            while pending and time.time() < deadline:
+                for ticket, status, arr, fin, user in srv.poll():
+                    i, inp, out, tag = pending.pop(ticket)
+                    done[i] = (status, out, tag)
+                time.sleep(0.001)
+            assert not pending, "requests did not complete"
+            stats = srv.stats()
+        finally:
+            srv.close()
+    finally:
+        ctx.set_host_access(0)
+    assert stats["error"] == 0
+    assert stats["budget"] == budget
+    assert 0 < stats["peak_bytes_in_flight"] <= budget
+    assert stats["budget_waits"] > 0  # admission was deferred on memory
+    assert total > 2 * budget
+    for i, q in enumerate(reqs):
+        status, out, tag = done[i]
+        o, n = q["off"], q["n"]
+        if q["op"] == 0:
+            assert status == 0, i
+            assert tag.tobytes() == ref[i][1], i
+            assert np.array_equal(out[:n], cts[o:o + n]), i
+        elif q["bad"]:
+            assert status == -3, i
+            assert not out[:n].any(), i
+        else:
+            assert status == 0, i
+            assert np.array_equal(out[:n], pts[o:o + n]), i

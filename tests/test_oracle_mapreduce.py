@@ -112,3 +112,20 @@ def test_planted_mistakes_are_detected(monkeypatch):
     monkeypatch.setattr(oracle, "combine", lambda h, a, b, n: comb(h, a, b, max(0, n - 1)))
     (dg, tag), = run([m], 64)
     assert dg == serial_digests(ct, 64) and tag != ref_tag
+
+
+def test_ciphertext_written_to_an_output_file():
+    r = random.Random(45)
+    msgs = [{"key": rnd(r, 32), "iv": rnd(r, 12), "aad": rnd(r, 9), "pt": rnd(r, n)} for n in (0, 33, 5000, 160)]
+    total = sum(len(m["pt"]) for m in msgs)
+    with mapreduce.HostInput(total) as src, mapreduce.HostInput(total) as dst:
+        spec, off = [], 0
+        for m in msgs:
+            src.array[off:off + len(m["pt"])] = np.frombuffer(m["pt"], dtype=np.uint8)
+            spec.append({"key": m["key"], "iv": m["iv"], "aad": m["aad"], "off": off, "len": len(m["pt"])})
+            off += len(m["pt"])
+        got = mapreduce.gcm_encrypt_digests(spec, src, chunk_bytes=64, workers=2, dest=dst)
+        for m, s_, (dg, tag) in zip(msgs, spec, got):
+            ct, ref_tag = oracle.gcm_encrypt(m["key"], m["iv"], m["aad"], m["pt"])
+            assert tag == ref_tag
+            assert bytes(dst.array[s_["off"]: s_["off"] + s_["len"]]) == ct
