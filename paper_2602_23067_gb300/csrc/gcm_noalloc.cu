@@ -15,6 +15,7 @@
 #include <mutex>
 #include <string>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "gcm_internal.h"
@@ -48,6 +49,37 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mu;
 uint8_t *g_na_ptr[NA_MAX_DEVICES] = {};
 int g_na_sms[NA_MAX_DEVICES] = {};
+unsigned long long g_na_ctx[NA_MAX_DEVICES] = {};  // context the set-up was done in
+
+// Identity of the calling thread's current CUDA context (driver entry points
+// cuCtxGetCurrent / cuCtxGetId, resolved once through the runtime); 0 when
+// there is none yet or the driver cannot tell.  A device reset or a new
+// primary context gets a new identity, so the set-up below is redone.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 thread_local std::string g_na_error;
 
@@ -77,10 +109,14 @@ uint32_t na_tile_log2(uint64_t M, int num_sms)
 // the fused kernel's shared-memory limit, and the AES round tables (built on
 // `stream`, which is then synchronised so that later calls on any stream see
 // them).
+// Set-up is per device and per CUDA context: the cache entry records the
+// context it was made in and is redone when the current context differs
+// (after cudaDeviceReset, for example).
 int na_setup(int dev, cudaStream_t stream, uint8_t **base, int *num_sms)
 {
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (g_na_ptr[dev]) {
+    unsigned long long cid = current_context_id();
+    if (g_na_ptr[dev] && cid != 0 && cid == g_na_ctx[dev]) {
         *base = g_na_ptr[dev];
         *num_sms = g_na_sms[dev];
         return GCM_OK;
@@ -88,6 +124,12 @@ int na_setup(int dev, cudaStream_t stream, uint8_t **base, int *num_sms)
     uint8_t *ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void **>(&ptr), g_noalloc_scratch);
     if (e != cudaSuccess) return na_cuda_fail(e, "cudaGetSymbolAddress of the static scratch");
+    cid = current_context_id();  // the runtime has bound a context by now
+    if (g_na_ptr[dev] == ptr && cid == g_na_ctx[dev]) {
+        *base = ptr;
+        *num_sms = g_na_sms[dev];
+        return GCM_OK;
+    }
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return na_cuda_fail(e, "cudaDeviceGetAttribute");
@@ -98,6 +140,7 @@ int na_setup(int dev, cudaStream_t stream, uint8_t **base, int *num_sms)
     if (e != cudaSuccess) return na_cuda_fail(e, "building the round tables in the static scratch");
     g_na_ptr[dev] = ptr;
     g_na_sms[dev] = sms;
+    g_na_ctx[dev] = cid;
     *base = ptr;
     *num_sms = sms;
     return GCM_OK;
