@@ -22,6 +22,12 @@ constexpr int SEGF_SIZES = 8;      // tile sizes 2^9 .. 2^16
 constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
 constexpr uint32_t BATCH_TILE_LOG2 = 16;  // tile size of the batched kernel (2^16 blocks)
 constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
+// Warps of the fused kernel that run their GHASH chains through the integer
+// field multiply instead of the table (a measured alternative; 0 = none).
+// Set at build time, e.g. GCMGPU_NVCC_FLAGS=-DGH_IMAD_WARPS=2.
+#ifndef GH_IMAD_WARPS
+#define GH_IMAD_WARPS 0
+#endif
 
 // Shared-memory map of the fused kernel (byte offsets into dynamic smem).
 constexpr uint32_t SM_T01 = 0;         // rows v: [T0[v] x 32 lanes | T1[v] x 32 lanes]

@@ -581,6 +581,20 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     bool have = false;
     uint32_t seg_len = 0;
     uint64_t dsum = 0;  // MODE_GCM_SUM: this lane's word sum (< 2^45 per tile)
+#if GH_IMAD_WARPS > 0
+    // Measured alternative (off by default): the last GH_IMAD_WARPS warps
+    // multiply their Horner chains by H^32 with the integer-product field
+    // multiply instead of the shared-memory table, to move GHASH work off the
+    // shared-memory pipe onto the logic and multiply pipes.  Bit-exact, but
+    // slower at every warp count tried.
+    const bool imad = (MODE == MODE_GCM || MODE == MODE_GCM_SUM) && warp >= KF_WARPS - GH_IMAD_WARPS;
+    bool poly = false;
+    gf128 accp = gf_zero(), h32 = gf_zero();
+    if (imad) {
+        const uint4 g = __ldg(reinterpret_cast<const uint4 *>(&km->h2k[GH_LOG2_STRIDE]));
+        h32.w[0] = g.x; h32.w[1] = g.y; h32.w[2] = g.z; h32.w[3] = g.w;
+    }
+#endif
 
     if (seg_hi > seg_lo) {
         seg_len = (uint32_t)(seg_hi - seg_lo);
@@ -650,9 +664,17 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
                     __stcs(out + d, ks);
                     if (MODE == MODE_GCM || MODE == MODE_GCM_SUM) {
                         const uint4 x = v.dec ? din : ks;
-                        uint4 m = ghash_mul_table(smem, acc, L);
-                        xor4(m, x);
-                        acc = m;
+#if GH_IMAD_WARPS > 0
+                        if (imad) {
+                            accp = gf_xor(gf_mul(accp, h32), gf_from_mem(x.x, x.y, x.z, x.w));
+                            poly = true;
+                        } else
+#endif
+                        {
+                            uint4 m = ghash_mul_table(smem, acc, L);
+                            xor4(m, x);
+                            acc = m;
+                        }
                         dlast = d;
                         have = true;
                         if (MODE == MODE_GCM_SUM) dsum += word_sum_be(x);
@@ -670,6 +692,10 @@ __device__ __forceinline__ void tile_body(uint8_t *smem, const MsgView &v, const
     // before the segment end, 1 <= e <= 32), reduce the warp, move the
     // warp's partial to the tile end, reduce the CTA.
     gf128 z = gf_zero();
+#if GH_IMAD_WARPS > 0
+    if (have && poly) z = gf_mul(accp, km->hpow[seg_len - dlast - 1]);
+    else
+#endif
     if (have) z = gf_mul(gf_from_mem(acc.x, acc.y, acc.z, acc.w), km->hpow[seg_len - dlast - 1]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1)
