@@ -17,9 +17,11 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libgcmgpu.so")
+PROBE_LIB = os.path.join(PKG, "libgcmprobe.so")  # microbenchmarks (probe_rates.cu), not the product
 BUILD_DIR = os.path.join(PKG, "_build")
 
 SOURCES = ["gcm_kernels.cu", "gcm_api.cu", "gcm_noalloc.cu", "gfc_fits.cu", "gcm_stream.cu", "gcm_batch.cu", "gcm_server.cu"]
+PROBE_SOURCE = "probe_rates.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -31,7 +33,7 @@ def _nvcc() -> str:
 
 
 def _inputs():
-    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
+    files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != PROBE_SOURCE]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     files += [os.path.join(PKG, "exports.map"), os.path.abspath(__file__)]
     return files
@@ -42,6 +44,22 @@ def up_to_date() -> bool:
         return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def build_probes(force: bool = False, verbose: bool = False) -> str:
+    """libgcmprobe.so: the rate microbenchmarks (one translation unit)."""
+    src = os.path.join(CSRC, PROBE_SOURCE)
+    if not force and os.path.exists(PROBE_LIB) and os.path.getmtime(PROBE_LIB) >= max(
+            os.path.getmtime(src), os.path.getmtime(os.path.abspath(__file__))):
+        return PROBE_LIB
+    tmp = PROBE_LIB + ".tmp.%d" % os.getpid()
+    cmd = [_nvcc(), "-shared"] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-o", tmp, src,
+                                         "-cudart", "static"]
+    if verbose:
+        print(" ".join(cmd), file=sys.stderr)
+    subprocess.check_call(cmd)
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -74,3 +92,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True))
+    print(build_probes(force="--force" in sys.argv, verbose=True))
