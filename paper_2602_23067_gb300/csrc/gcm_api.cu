@@ -113,16 +113,24 @@ struct Scratch {
 
 // The ticket word of `s` for fused launches that finish their message, or
 // null when every slot is taken (the call then uses the combine kernel).
+// Slots are keyed by the stream's id, which the runtime never reuses (a
+// stream handle can be reused after cudaStreamDestroy while the destroyed
+// stream's work is still running, so the handle cannot be the key).
 uint32_t *ticket_for(gcm_ctx *ctx, cudaStream_t s)
 {
     if (!ctx->tickets) return nullptr;
+    unsigned long long id = 0;
+    if (cudaStreamGetId(s, &id) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
     const std::thread::id who = (s == cudaStreamPerThread) ? std::this_thread::get_id() : std::thread::id();
     std::lock_guard<std::mutex> lk(ctx->mu);
-    auto it = ctx->ticket_slot.find({s, who});
+    auto it = ctx->ticket_slot.find({id, who});
     if (it != ctx->ticket_slot.end()) return ctx->tickets + it->second;
     const int n = (int)ctx->ticket_slot.size();
     if (n >= gcm_ctx::TICKET_SLOTS) return nullptr;
-    ctx->ticket_slot.emplace(std::make_pair(s, who), n);
+    ctx->ticket_slot.emplace(std::make_pair(id, who), n);
     return ctx->tickets + n;
 }
 

@@ -89,12 +89,14 @@ struct gcm_ctx {
     int aes_impl = 0;
     // Ticket words of fused launches that finish their own message (the
     // last CTA runs the combine and the tag): one zero word per stream the
-    // calls use, so that only launches ordered on one stream share a word; a
-    // launch leaves its word at zero.  The per-thread default stream is one
-    // handle for many streams, so its words are per calling thread too.
+    // calls use (keyed by the runtime's stream id, never reused), so that
+    // only launches ordered on one stream share a word; a launch leaves its
+    // word at zero.  The per-thread default stream is one handle for many
+    // streams, so its words are per calling thread too.  Once every slot is
+    // taken, calls on further streams use the separate combine kernel.
     static constexpr int TICKET_SLOTS = 4096;
     uint32_t *tickets = nullptr;
-    std::map<std::pair<cudaStream_t, std::thread::id>, int> ticket_slot;  // guarded by mu
+    std::map<std::pair<unsigned long long, std::thread::id>, int> ticket_slot;  // guarded by mu
 };
 
 namespace gcmgpu {

@@ -154,3 +154,50 @@ def test_both_sides_of_the_finish_boundary(torch_cuda):
             gh = ctx.ghash_device(key, a, ct)
             torch.cuda.synchronize()
             assert host(gh) == oracle.ghash(h, blob), tiles
+
+
+def test_streams_destroyed_with_work_in_flight_and_per_thread_streams(torch_cuda):
+    # Stream handles can be reused once a stream is destroyed, even while its
+    # work still runs; the per-thread default stream is one handle for one
+    # stream per thread.  Calls on both kinds must finish correctly.
+    import threading
+
+    torch = torch_cuda
+    from paper_2602_23067_gb300 import Context
+
+    r = random.Random(65)
+    cases = [(rnd(r, 16), rnd(r, 12), rnd(r, 20), rnd(r, 4096 * (3 + k % 5) + k)) for k in range(24)]
+    refs = [oracle.gcm_encrypt(*c) for c in cases]
+    with Context(0) as ctx:
+        outs = []
+        for k, (key, iv, aad, pt) in enumerate(cases[:12]):
+            st = torch.cuda.Stream()  # released (destroyed) when dropped below
+            a, p = dev(torch, aad), dev(torch, pt)
+            torch.cuda.synchronize()
+            ct, tag = ctx.encrypt_device(key, iv, a, p, stream=st)
+            outs.append((ct, tag, a, p))
+            del st
+        torch.cuda.synchronize()
+        for (ct, tag, _, _), (ref_ct, ref_tag) in zip(outs, refs[:12]):
+            assert host(tag) == ref_tag and host(ct) == ref_ct
+
+        per_thread = 2  # cudaStreamPerThread
+        res = {}
+
+        def worker(tid):
+            for k in range(tid, 12, 2):
+                key, iv, aad, pt = cases[12 + k]
+                a, p = dev(torch, aad), dev(torch, pt)
+                torch.cuda.synchronize()
+                ct, tag = ctx.encrypt_device(key, iv, a, p, stream=per_thread)
+                res[12 + k] = (ct, tag)
+
+        th = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        torch.cuda.synchronize()
+        for k in range(12, 24):
+            ct, tag = res[k]
+            assert host(tag) == refs[k][1] and host(ct) == refs[k][0], k
