@@ -59,14 +59,28 @@ def _host_buf(data) -> Tuple[int, int, object]:
     raise TypeError("unsupported host buffer type %r" % type(data))
 
 
+def _key_arg(b) -> Tuple[object, int]:
+    """A host key or IV for a direct library call: bytes objects are passed
+    as they are (ctypes hands over a pointer to their immutable buffer for
+    the duration of the call), anything else through _host_buf."""
+    if type(b) is bytes:
+        return b, len(b)
+    p, n, _ = _host_buf(b)
+    return p, n
+
+
 def _dev_buf(t) -> Tuple[int, int]:
     if t is None:
         return 0, 0
-    if not hasattr(t, "data_ptr") or not t.is_cuda:
+    try:
+        cuda, contig = t.is_cuda, t.is_contiguous()
+    except AttributeError:
+        raise TypeError("device mode expects CUDA tensors") from None
+    if not cuda:
         raise TypeError("device mode expects CUDA tensors")
-    if not t.is_contiguous():
+    if not contig:
         raise ValueError("tensors must be contiguous")
-    return t.data_ptr(), t.numel() * t.element_size()
+    return t.data_ptr(), t.nbytes
 
 
 def _stream_handle(stream) -> Optional[int]:
@@ -107,14 +121,15 @@ class Context:
     # -- device-resident data (torch CUDA uint8 tensors) -------------------
     def encrypt_device(self, key: bytes, iv: bytes, aad, pt, ct=None, tag=None, stream=None):
         """Enqueue GCM-AE on device tensors; returns (ct, tag) tensors."""
-        import torch
+        if ct is None or tag is None:
+            import torch
 
-        if ct is None:
-            ct = torch.empty_like(pt)
-        if tag is None:
-            tag = torch.empty(16, dtype=torch.uint8, device=pt.device)
-        kp, kl, kk = _host_buf(key)
-        ip, il, ik = _host_buf(iv)
+            if ct is None:
+                ct = torch.empty_like(pt)
+            if tag is None:
+                tag = torch.empty(16, dtype=torch.uint8, device=pt.device)
+        kp, kl = _key_arg(key)
+        ip, il = _key_arg(iv)
         ap, al = _dev_buf(aad)
         pp, pl = _dev_buf(pt)
         cp, cl = _dev_buf(ct)
@@ -128,12 +143,12 @@ class Context:
     def decrypt_verify_device(self, key: bytes, iv: bytes, aad, ct, tag, pt=None, stream=None):
         """GCM-AD on device tensors.  Raises GcmError(GCM_ERR_AUTH) on a tag
         mismatch, after the output has been zero-filled on the device."""
-        import torch
-
         if pt is None:
+            import torch
+
             pt = torch.empty_like(ct)
-        kp, kl, kk = _host_buf(key)
-        ip, il, ik = _host_buf(iv)
+        kp, kl = _key_arg(key)
+        ip, il = _key_arg(iv)
         ap, al = _dev_buf(aad)
         cp, cl = _dev_buf(ct)
         tp, tl = _dev_buf(tag)

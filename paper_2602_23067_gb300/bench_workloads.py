@@ -519,9 +519,13 @@ def run_small(args, cpu_baseline=None, check=None):
     tags = torch.empty((n_msgs, 16), dtype=torch.uint8, device="cuda")
     d_aad = torch.frombuffer(bytearray(aad), dtype=torch.uint8).cuda()
 
+    # Per-message views made once, so that the timed calls measure the
+    # library calls rather than tensor indexing.
+    pv, cv, tv, bv = ([x[i] for i in range(n_msgs)] for x in (pts, cts, tags, backs))
+
     def step(i):
-        ctx.encrypt_device(key, iv, d_aad, pts[i], ct=cts[i], tag=tags[i], stream=stream)
-        ctx.decrypt_verify_device(key, iv, d_aad, cts[i], tags[i], pt=backs[i], stream=stream)
+        ctx.encrypt_device(key, iv, d_aad, pv[i], ct=cv[i], tag=tv[i], stream=stream)
+        ctx.decrypt_verify_device(key, iv, d_aad, cv[i], tv[i], pt=bv[i], stream=stream)
 
     step(0)
     torch.cuda.synchronize()

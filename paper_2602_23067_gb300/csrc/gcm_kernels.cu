@@ -453,6 +453,32 @@ __device__ __forceinline__ void stage_ghash_table(uint8_t *smem, const KeyMat *k
     for (int i = threadIdx.x; i < GTAB_ENTRIES; i += blockDim.x) sg[i] = __ldg(&g[i]);
 }
 
+// Both tables of the fused kernel (KF_THREADS threads), with every global
+// load of a thread issued before its first shared-memory store, so that the
+// staging costs about one memory round trip instead of one per loop trip.
+__device__ __forceinline__ void stage_fused_tables(uint8_t *smem, const DevTables *tabs, const KeyMat *km)
+{
+    constexpr int RT = 8192 / KF_THREADS, GT = GTAB_ENTRIES / KF_THREADS;
+    const uint32_t *tt = tabs->ttab;
+    const uint4 *g = km->gtab;
+    uint32_t w[RT];
+    uint4 e[GT];
+#pragma unroll
+    for (int k = 0; k < RT; k++) {
+        const int q = threadIdx.x + k * KF_THREADS;
+        const int region = q >> 12, v = (q >> 4) & 255, odd = (q >> 3) & 1;
+        w[k] = __ldg(&tt[(2 * region + odd) * 256 + v]);
+    }
+#pragma unroll
+    for (int k = 0; k < GT; k++) e[k] = __ldg(&g[threadIdx.x + k * KF_THREADS]);
+    uint4 *s128 = reinterpret_cast<uint4 *>(smem);
+    uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
+#pragma unroll
+    for (int k = 0; k < RT; k++) s128[threadIdx.x + k * KF_THREADS] = make_uint4(w[k], w[k], w[k], w[k]);
+#pragma unroll
+    for (int k = 0; k < GT; k++) sg[threadIdx.x + k * KF_THREADS] = e[k];
+}
+
 // H^((15-w) * S) for every warp w, S = 2^(tile_log2 - 4): moves a warp's
 // segment partial to the tile end.  Lane 0 of each warp copies its own from
 // the key material.
@@ -776,7 +802,15 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
     const KeyMat *km = p.km;
     uint32_t *sej0 = reinterpret_cast<uint32_t *>(smem + SM_RED);
     int32_t *sfail = reinterpret_cast<int32_t *>(smem + SM_RED + 16);
-    if (warp == 0) {
+    // The tree's buffers take the place of the GHASH table (no longer read),
+    // so the last warp can compute E_K(J0) from the round tables while the
+    // other warps stage the partials and the multipliers.
+    gf128 *sbuf0 = reinterpret_cast<gf128 *>(smem + SM_GTAB);
+    gf128 *sbuf1 = reinterpret_cast<gf128 *>(smem + SM_GTAB + 16 * FINISH_MAX_TILES);
+    gf128 *smult = reinterpret_cast<gf128 *>(smem + SM_GTAB + 32 * FINISH_MAX_TILES);
+    uint64_t *wscr = reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp;
+    const uint64_t K = p.K;
+    if (warp == nwarps - 1) {
         uint4 e = make_uint4(0u, 0u, 0u, 0u);
         if (MODE != MODE_GHASH) {
             if (p.j0_given) {
@@ -795,17 +829,14 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
             sej0[0] = e.x; sej0[1] = e.y; sej0[2] = e.z; sej0[3] = e.w;
             *sfail = 0;
         }
+    } else {
+        const int ts = t, nts = blockDim.x - 32;
+        for (uint64_t i = ts; i < K; i += nts)
+            for (int k = 0; k < 4; k++) sbuf1[i].w[k] = __ldcg(&p.partials[i].w[k]);
+        if (ts < H2K_COUNT && (uint32_t)ts + p.tile_log2 < (uint32_t)H2K_COUNT)
+            smult[ts] = km->h2k[p.tile_log2 + ts];
+        if (ts == H2K_COUNT) smult[H2K_COUNT] = km->H;
     }
-    __syncthreads();  // the round tables are no longer read below
-    gf128 *sbuf0 = reinterpret_cast<gf128 *>(smem);
-    gf128 *sbuf1 = reinterpret_cast<gf128 *>(smem + 16 * FINISH_MAX_TILES);
-    gf128 *smult = reinterpret_cast<gf128 *>(smem + 32 * FINISH_MAX_TILES);
-    uint64_t *wscr = reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp;
-    const uint64_t K = p.K;
-    for (uint64_t i = t; i < K; i += blockDim.x)
-        for (int k = 0; k < 4; k++) sbuf1[i].w[k] = __ldcg(&p.partials[i].w[k]);
-    if (t < H2K_COUNT && (uint32_t)t + p.tile_log2 < (uint32_t)H2K_COUNT) smult[t] = km->h2k[p.tile_log2 + t];
-    if (t == H2K_COUNT) smult[H2K_COUNT] = km->H;
     __syncthreads();
     uint64_t cnt = K;
     int level = 0;
@@ -895,8 +926,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) fused_kernel(const __grid_const
     extern __shared__ __align__(1024) uint8_t smem[];
     const uint8_t *t01 = smem + SM_T01;
     const uint8_t *t23 = smem + SM_T23;
-    stage_round_tables(smem, p.tabs);
-    stage_ghash_table(smem, p.km);
+    stage_fused_tables(smem, p.tabs, p.km);
     stage_segment_factors(smem, p.km, p.tile_log2);
     uint32_t rk[4 * (NR + 1)];
 #pragma unroll
