@@ -208,7 +208,8 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
     if (slot < 0) {
         if (C.size() < ctx->key_cache_cap) {
             gcm_ctx::KeyCacheEntry e;
-            if (cudaMalloc(reinterpret_cast<void **>(&e.km), sizeof(KeyMat)) != cudaSuccess) {
+            // The entry's KeyMat is followed by its flat-reduce weights.
+            if (cudaMalloc(reinterpret_cast<void **>(&e.km), sizeof(KeyMat) + sizeof(KeyFin)) != cudaSuccess) {
                 cudaGetLastError();
                 return -1;
             }
@@ -239,6 +240,7 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
     }
     auto &e = C[slot];
     ks.km = e.km;
+    ks.fin = reinterpret_cast<KeyFin *>(e.km + 1);
     if (fresh) {
         memcpy(e.key, ks.key, ks.key_len);
         e.key_len = ks.key_len;
@@ -297,9 +299,9 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     while ((1ull << levels) < K) levels++;
     if (lg + levels >= (uint32_t)H2K_COUNT) return fail(GCM_ERR_LENGTH_LIMIT, "message too long for the power table");
 
-    // Scratch layout: KeyMat | MsgMat | partials[K] | tree scratch | IV copy
+    // Scratch layout: KeyMat + KeyFin | MsgMat | partials[K] | tree scratch | IV copy
     const size_t off_km = 0;
-    const size_t off_mm = align_up(off_km + sizeof(KeyMat), 256);
+    const size_t off_mm = align_up(off_km + sizeof(KeyMat) + sizeof(KeyFin), 256);
     const size_t off_part = align_up(off_mm + sizeof(MsgMat), 256);
     const size_t off_tree = align_up(off_part + (size_t)K * sizeof(gf128), 256);
     const size_t off_iv = align_up(off_tree + (size_t)(K / 2 + 1) * sizeof(gf128), 256);
@@ -336,6 +338,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         km = ks.km;
     } else {
         ks.km = km;
+        ks.fin = reinterpret_cast<KeyFin *>(km + 1);
         e = launch_key_setup(ks, s);
         if (e != cudaSuccess) return cuda_fail(e, "key setup launch");
         setup_launches = 1;
@@ -389,6 +392,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
     if (can_finish && K >= 1 && K <= FINISH_MAX_TILES && M <= FINISH_MAX_BLOCKS) {
         kf.ticket = ticket_for(ctx, s);
         if (kf.ticket) {
+            kf.fin = reinterpret_cast<const KeyFin *>(km + 1);
             kf.tag_out = decrypt ? nullptr : tag_dev;
             kf.tag_expected = decrypt ? tag_dev : nullptr;
             kf.status = status_dev;

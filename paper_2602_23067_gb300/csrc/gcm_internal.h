@@ -60,6 +60,16 @@ struct KeyMat {
     uint4 gtab[GTAB_ENTRIES];   // entry v*16+k = (byte v at position k) * H^32, memory words
 };
 
+// Weights of the flat reduce that finishes a message of at most 1024 tiles
+// of 2^lg blocks inside the fused launch: the partial of the tile g tiles
+// before the last one moves to the sequence end by
+// H^(2^lg * g) = w1[g mod 32] * w2[g / 32].  Built by the single-message key
+// setup only, and stored right after that path's KeyMat.
+struct KeyFin {
+    gf128 w1[SEGF_SIZES][32];  // [lg - SEGF_MIN_LOG2][j] = H^(2^lg * j)
+    gf128 w2[SEGF_SIZES][32];  // [lg - SEGF_MIN_LOG2][q] = H^(2^lg * 32 q)
+};
+
 // Per-message material.
 struct MsgMat {
     uint32_t j0[4];   // pre-counter block J0, memory words
@@ -83,6 +93,7 @@ struct KsParams {
     KeyMat *km;
     MsgMat *mm;
     const DevTables *tabs;
+    KeyFin *fin;                // non-null: also build the flat-reduce weights here
 };
 
 struct KfParams {
@@ -111,6 +122,7 @@ struct KfParams {
     // combine, the length block, the tag and the verify gate.  ticket is a
     // zero word that only launches on one stream share (left at zero).
     uint32_t *ticket;       // null: a separate combine kernel follows
+    const KeyFin *fin;      // flat-reduce weights of the key (with ticket)
     uint8_t *tag_out;       // 16 bytes (device): the tag, or GHASH_H(A, C) in mode 2
     const uint8_t *tag_expected;  // 16 bytes (device) for decryption, else null
     int32_t *status;        // device verdict word (decryption), may be null

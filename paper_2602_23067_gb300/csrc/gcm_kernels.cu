@@ -103,7 +103,7 @@ __device__ int key_expand_words(const uint8_t *key, int key_len, const uint8_t *
 // The whole per-key / per-message setup, run by one CTA of 256 threads.
 // iv points to iv_len bytes (device or kernel-parameter memory).
 __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8_t *iv, uint32_t iv_len, KeyMat *km,
-                               MsgMat *mm, const DevTables *tabs)
+                               MsgMat *mm, const DevTables *tabs, KeyFin *fin = nullptr)
 {
     __shared__ uint8_t sbox[256];
     __shared__ uint32_t rkw[60];
@@ -195,6 +195,20 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         for (int b = 0; b < KF_LOG2_WARPS; b++) f = gf_mul(f, ((steps >> b) & 1) ? sh2k[base + b] : one);
         km->segf[sz][w] = f;
     }
+    if (fin) {
+        // Flat-reduce weights for tiles of 2^lg blocks, lg = 9..16: entry j of
+        // w1 is H^(2^lg * j) (bits of j select H^(2^(lg+b))), entry q of w2
+        // is H^(2^lg * 32 q) (H^(2^(lg+5+b))); two entries per thread.
+        for (int idx = t; idx < 2 * SEGF_SIZES * 32; idx += blockDim.x) {
+            const int which = idx / (SEGF_SIZES * 32), r = idx % (SEGF_SIZES * 32);
+            const int sz = r / 32, e = r % 32;
+            const int base = SEGF_MIN_LOG2 + sz + (which ? 5 : 0);
+            gf128 f = one;
+            for (int b = 0; b < 5; b++) f = gf_mul(f, ((e >> b) & 1) ? sh2k[base + b] : one);
+            if (which) fin->w2[sz][e] = f;
+            else fin->w1[sz][e] = f;
+        }
+    }
     __syncthreads();
     // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32.
     // Bit b of v (LSB = 0) is the coefficient of x^(8k + 7 - b).
@@ -213,7 +227,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
 __global__ void __launch_bounds__(256) key_setup_kernel(const __grid_constant__ KsParams p)
 {
     const uint8_t *iv = (p.iv_len <= IV_INLINE_MAX) ? p.iv_inline : p.iv_dev;
-    key_setup_body(p.key, p.key_len, iv, p.iv_len, p.km, p.mm, p.tabs);
+    key_setup_body(p.key, p.key_len, iv, p.iv_len, p.km, p.mm, p.tabs, p.fin);
 }
 
 // ---------------------------------------------------------------------
@@ -838,37 +852,35 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
         if (ts == H2K_COUNT) smult[H2K_COUNT] = km->H;
     }
     __syncthreads();
-    uint64_t cnt = K;
-    int level = 0;
-    const gf128 *src = sbuf1;
-    bool reversed = true;
-    gf128 *dst = sbuf0;
-    while (cnt > 1) {
-        const uint64_t half = (cnt + 1) / 2;
-        const gf128 mult = smult[level];
-        if (half > (uint64_t)nwarps * 4) {
-            for (uint64_t g = t; g < half; g += blockDim.x) {
-                const uint64_t ri = 2 * g, li = 2 * g + 1;
-                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
-                if (li < cnt) v = gf_xor(gf_mul(reversed ? src[cnt - 1 - li] : src[li], mult), v);
-                dst[g] = v;
-            }
-        } else {
-            for (uint64_t g = warp; g < half; g += nwarps) {
-                const uint64_t ri = 2 * g, li = 2 * g + 1;
-                gf128 v = reversed ? src[cnt - 1 - ri] : src[ri];
-                if (li < cnt) v = gf_xor(gf_mul_warp(reversed ? src[cnt - 1 - li] : src[li], mult, wscr), v);
-                if (lane == 0) dst[g] = v;
-            }
-        }
-        __syncthreads();
-        const gf128 *done = dst;
-        dst = (dst == sbuf0) ? sbuf1 : sbuf0;
-        src = done;
-        reversed = false;
-        cnt = half;
-        level++;
+    // Flat reduce: with g = K - 1 - i the distance of partial i from the last
+    // tile, G = sum_g P_i * H^(2^lg g) = sum_q (sum_j P * w1[j]) * w2[q]
+    // (g = 32 q + j): one product per partial, a warp XOR, one product per
+    // group of 32.  Thread t handles g = t and g = t + 512 (K <= 1024).
+    const int sz = (int)p.tile_log2 - SEGF_MIN_LOG2;
+    gf128 *sgrp = sbuf0;  // group sums S_q, q < 32
+    for (int pass = 0; pass < (int)((FINISH_MAX_TILES + blockDim.x - 1) / blockDim.x); pass++) {
+        const uint64_t g = (uint64_t)t + (uint64_t)pass * blockDim.x;
+        gf128 u = gf_zero();
+        if (g < K) u = gf_mul(sbuf1[K - 1 - g], p.fin->w1[sz][g & 31]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) u.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, u.w[k], off);
+        if (lane == 0 && (g >> 5) < 32) sgrp[g >> 5] = u;  // the warp of g holds group g / 32
     }
+    __syncthreads();
+    const uint64_t ngrp = (K + 31) / 32;
+    gf128 *src = sbuf1;  // src[0] = G after the reduce below
+    if (warp == 0) {
+        gf128 u = gf_zero();
+        if ((uint64_t)lane < ngrp) u = gf_mul(sgrp[lane], p.fin->w2[sz][lane]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 4; k++) u.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, u.w[k], off);
+        if (lane == 0) src[0] = u;
+    }
+    __syncthreads();
     if (MODE == MODE_GCM_SUM) {
         uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
         uint64_t acc = 0;
