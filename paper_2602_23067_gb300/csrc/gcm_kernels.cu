@@ -816,12 +816,12 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
     const KeyMat *km = p.km;
     uint32_t *sej0 = reinterpret_cast<uint32_t *>(smem + SM_RED);
     int32_t *sfail = reinterpret_cast<int32_t *>(smem + SM_RED + 16);
-    // The tree's buffers take the place of the GHASH table (no longer read),
-    // so the last warp can compute E_K(J0) from the round tables while the
-    // other warps stage the partials and the multipliers.
-    gf128 *sbuf0 = reinterpret_cast<gf128 *>(smem + SM_GTAB);
-    gf128 *sbuf1 = reinterpret_cast<gf128 *>(smem + SM_GTAB + 16 * FINISH_MAX_TILES);
-    gf128 *smult = reinterpret_cast<gf128 *>(smem + SM_GTAB + 32 * FINISH_MAX_TILES);
+    // The reduce's buffers take the place of the GHASH table (no longer
+    // read), so the last warp can compute E_K(J0) from the round tables while
+    // the other warps stage the partials and H.
+    gf128 *sgrp = reinterpret_cast<gf128 *>(smem + SM_GTAB);  // group sums, then G
+    gf128 *spart = reinterpret_cast<gf128 *>(smem + SM_GTAB + 16 * FINISH_MAX_TILES);
+    gf128 *sH = reinterpret_cast<gf128 *>(smem + SM_GTAB + 32 * FINISH_MAX_TILES);
     uint64_t *wscr = reinterpret_cast<uint64_t *>(smem + SM_WSCR) + 16 * warp;
     const uint64_t K = p.K;
     if (warp == nwarps - 1) {
@@ -844,12 +844,9 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
             *sfail = 0;
         }
     } else {
-        const int ts = t, nts = blockDim.x - 32;
-        for (uint64_t i = ts; i < K; i += nts)
-            for (int k = 0; k < 4; k++) sbuf1[i].w[k] = __ldcg(&p.partials[i].w[k]);
-        if (ts < H2K_COUNT && (uint32_t)ts + p.tile_log2 < (uint32_t)H2K_COUNT)
-            smult[ts] = km->h2k[p.tile_log2 + ts];
-        if (ts == H2K_COUNT) smult[H2K_COUNT] = km->H;
+        for (uint64_t i = t; i < K; i += blockDim.x - 32)
+            for (int k = 0; k < 4; k++) spart[i].w[k] = __ldcg(&p.partials[i].w[k]);
+        if (t == 0) *sH = km->H;
     }
     __syncthreads();
     // Flat reduce: with g = K - 1 - i the distance of partial i from the last
@@ -857,11 +854,10 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
     // (g = 32 q + j): one product per partial, a warp XOR, one product per
     // group of 32.  Thread t handles g = t and g = t + 512 (K <= 1024).
     const int sz = (int)p.tile_log2 - SEGF_MIN_LOG2;
-    gf128 *sgrp = sbuf0;  // group sums S_q, q < 32
     for (int pass = 0; pass < (int)((FINISH_MAX_TILES + blockDim.x - 1) / blockDim.x); pass++) {
         const uint64_t g = (uint64_t)t + (uint64_t)pass * blockDim.x;
         gf128 u = gf_zero();
-        if (g < K) u = gf_mul(sbuf1[K - 1 - g], p.fin->w1[sz][g & 31]);
+        if (g < K) u = gf_mul(spart[K - 1 - g], p.fin->w1[sz][g & 31]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
@@ -870,17 +866,14 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
     }
     __syncthreads();
     const uint64_t ngrp = (K + 31) / 32;
-    gf128 *src = sbuf1;  // src[0] = G after the reduce below
+    gf128 G = gf_zero();  // meaningful in warp 0
     if (warp == 0) {
-        gf128 u = gf_zero();
-        if ((uint64_t)lane < ngrp) u = gf_mul(sgrp[lane], p.fin->w2[sz][lane]);
+        if ((uint64_t)lane < ngrp) G = gf_mul(sgrp[lane], p.fin->w2[sz][lane]);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int k = 0; k < 4; k++) u.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, u.w[k], off);
-        if (lane == 0) src[0] = u;
+            for (int k = 0; k < 4; k++) G.w[k] ^= __shfl_xor_sync(0xFFFFFFFFu, G.w[k], off);
     }
-    __syncthreads();
     if (MODE == MODE_GCM_SUM) {
         uint64_t *dred = reinterpret_cast<uint64_t *>(smem + SM_DSUM);
         uint64_t acc = 0;
@@ -896,14 +889,13 @@ __device__ __noinline__ void finish_message(uint8_t *smem, const KfParams &p)
         }
     }
     if (warp == 0) {
-        const gf128 s = src[0];
         gf128 lb;
         const uint64_t abits = p.aad_len * 8u, cbits = p.len * 8u;
         lb.w[0] = (uint32_t)(abits >> 32);
         lb.w[1] = (uint32_t)abits;
         lb.w[2] = (uint32_t)(cbits >> 32);
         lb.w[3] = (uint32_t)cbits;
-        const gf128 gh = gf_mul_warp(gf_xor(s, lb), smult[H2K_COUNT], wscr);
+        const gf128 gh = gf_mul_warp(gf_xor(G, lb), *sH, wscr);
         if (lane == 0) {
             const uint4 gm = gf_to_mem(gh);
             const uint32_t tw[4] = {gm.x ^ sej0[0], gm.y ^ sej0[1], gm.z ^ sej0[2], gm.w ^ sej0[3]};
