@@ -91,11 +91,13 @@ int size_class(uint64_t M)
 }
 
 // Tile sizes found by gcm_ctx_autotune on a GB300 (152 SMs, compute
-// capability 10.3) for AES-256-GCM, 16 KiB .. 1 GiB, indexed by
-// floor(log2(blocks)); installed by default on that device.  Medium messages
-// prefer about one tile per SM over the rule's four.
+// capability 10.3), 16 KiB .. 1 GiB, indexed by floor(log2(blocks));
+// installed by default on that device.  AES-128 and AES-256 give the same
+// table since messages of up to 1024 tiles finish inside the fused launch
+// (up to 4 MiB the smallest tiles win: more CTAs, no combine launch).
+// Medium messages prefer about one tile per SM over the rule's four.
 const uint8_t kTunedGB300[64] = {
-    0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  9,  9,  9,  9,  9,  9,  10, 10, 11, 11, 13, 13,
+    0,  0,  0,  0,  0,  0,  0,  0,  0,  0,  9,  9,  9,  9,  9,  9,  9,  9,  11, 11, 13, 13,
     15, 15, 14, 14, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16,
     16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16, 16};
 

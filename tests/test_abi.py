@@ -75,6 +75,16 @@ def test_host_alloc_argument_errors(native):
     assert native.lib.gcm_host_free(None) == native.GCM_OK
 
 
+def test_server_admission_argument_errors(native):
+    # gcm_server_admission checks its server argument before anything else.
+    import ctypes
+
+    b, peak, waits = ctypes.c_size_t(7), ctypes.c_size_t(7), ctypes.c_uint64(7)
+    rc = native.lib.gcm_server_admission(None, ctypes.byref(b), ctypes.byref(peak), ctypes.byref(waits))
+    assert rc == native.GCM_ERR_INVALID_ARG
+    assert (b.value, peak.value, waits.value) == (7, 7, 7)
+
+
 def build_c_consumer(out_dir):
     """Compiles tests/abi_consumer.c (C99, warnings as errors) against the
     header and links it to the library; returns the executable's path."""

@@ -201,3 +201,51 @@ def test_streams_destroyed_with_work_in_flight_and_per_thread_streams(torch_cuda
         for k in range(12, 24):
             ct, tag = res[k]
             assert host(tag) == refs[k][1] and host(ct) == refs[k][0], k
+
+
+def test_block_limit_of_the_finish_and_a_64_mib_zero_fill(torch_cuda):
+    # Tiles forced to 2^13 blocks: a sequence of exactly 2^22 blocks (512
+    # tiles, 64 MiB) is finished inside the fused launch -- including, for a
+    # tampered tag, the zero-fill of the whole payload by the finishing CTA --
+    # while 2^22 + 16 blocks go through the combine and zero-fill kernels.
+    # The oracle runs chunk by chunk on the host cores.
+    torch = torch_cuda
+    from oracle import mapreduce
+    from paper_2602_23067_gb300 import Context, GcmError, _native
+
+    r = random.Random(66)
+    with Context(0) as ctx:
+        ctx.set_tile_log2(13)
+        _native.gcm_profile_enable(ctx.handle, True)
+        for extra, enc_launches, dec_launches in ((0, 1, 1), (16, 2, 3)):
+            key, iv, aad = rnd(r, 32), rnd(r, 12), rnd(r, 32)
+            n = 16 * ((1 << 22) - 2 + extra) - 3  # AAD: 2 blocks; last payload block partial
+            g = torch.Generator(device="cuda")
+            g.manual_seed(66 + extra)
+            pt = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g)
+            with mapreduce.HostInput(n) as src, mapreduce.HostInput(n) as dst:
+                torch.from_numpy(src.array).copy_(pt)
+                (ref_dg, ref_tag), = mapreduce.gcm_encrypt_digests(
+                    [{"key": key, "iv": iv, "aad": aad, "off": 0, "len": n}], src, chunk_bytes=4 << 20, dest=dst)
+                ref_ct = torch.from_numpy(dst.array.copy()).cuda()
+            a = dev(torch, aad)
+            ctx.encrypt_device(key, iv, a, pt)  # key setup (cached afterwards)
+            torch.cuda.synchronize()
+            launches(ctx)
+            ct, tag = ctx.encrypt_device(key, iv, a, pt)
+            torch.cuda.synchronize()
+            assert launches(ctx) == enc_launches, extra
+            assert host(tag) == ref_tag, extra
+            assert torch.equal(ct, ref_ct), extra
+            bad = bytearray(ref_tag)
+            bad[0] ^= 0x01
+            out = torch.full((n,), 0x5A, dtype=torch.uint8, device="cuda")
+            with pytest.raises(GcmError):
+                ctx.decrypt_verify_device(key, iv, a, ref_ct, dev(torch, bytes(bad)), pt=out)
+            torch.cuda.synchronize()
+            assert launches(ctx) == dec_launches, extra
+            assert int(torch.count_nonzero(out).item()) == 0, extra
+            back = ctx.decrypt_verify_device(key, iv, a, ref_ct, dev(torch, ref_tag), pt=out)
+            torch.cuda.synchronize()
+            assert torch.equal(back, pt), extra
+            del pt, ct, ref_ct, out
