@@ -114,13 +114,20 @@ struct Scratch {
 };
 
 // The ticket word of `s` for fused launches that finish their message, or
-// null when every slot is taken (the call then uses the combine kernel).
-// Slots are keyed by the stream's id, which the runtime never reuses (a
-// stream handle can be reused after cudaStreamDestroy while the destroyed
-// stream's work is still running, so the handle cannot be the key).
+// null when every slot is taken or `s` is being captured into a graph (the
+// call then uses the combine kernel: replays of a graph on several streams
+// at once would share one word).  Slots are keyed by the stream's id, which
+// the runtime never reuses (a stream handle can be reused after
+// cudaStreamDestroy while the destroyed stream's work is still running, so
+// the handle cannot be the key).
 uint32_t *ticket_for(gcm_ctx *ctx, cudaStream_t s)
 {
     if (!ctx->tickets) return nullptr;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
     unsigned long long id = 0;
     if (cudaStreamGetId(s, &id) != cudaSuccess) {
         cudaGetLastError();
@@ -255,8 +262,10 @@ int key_cache_acquire(gcm_ctx *ctx, KsParams &ks, cudaStream_t s, cudaError_t &e
             return -1;
         }
     } else {
-        // With a 96-bit IV the caller forms J0 on the host and the combine
-        // kernel derives E_K(J0), so nothing per message is needed here.
+        // With a 96-bit IV the caller forms J0 on the host and the kernel
+        // that computes the tag (the finishing CTA of the fused launch, or
+        // the combine kernel) derives E_K(J0), so nothing per message is
+        // needed here.
         err = cudaStreamWaitEvent(s, e.ready, 0);
         if (err == cudaSuccess && ks.iv_len != 12) {
             err = launch_msg_only(ks, s);
@@ -388,7 +397,7 @@ int enqueue_device(gcm_ctx *ctx, const uint8_t *key, size_t key_len, const uint8
         kf.j0[3] = 0x01000000u;
     }
     // Messages of a few tiles are finished by the fused launch itself (its
-    // last CTA runs the tree, the tag and the verify gate): no combine or
+    // last CTA runs the reduce, the tag and the verify gate): no combine or
     // zero-fill launch follows.
     const bool can_finish = (mode == 2) || (mode != 1 && ctx->aes_impl == 0);
     if (can_finish && K >= 1 && K <= FINISH_MAX_TILES && M <= FINISH_MAX_BLOCKS) {
