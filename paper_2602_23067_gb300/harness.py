@@ -13,7 +13,6 @@ import os
 import statistics
 import subprocess
 import threading
-from typing import Optional
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 FALLBACK_HBM_GBS = 6800.0
