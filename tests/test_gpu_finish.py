@@ -1,6 +1,6 @@
-"""Messages finished inside the fused launch (the last CTA runs the tree
-combine, the length block, the tag and the verify gate) against the oracle,
-and the boundary to the separate combine kernel.
+"""Messages finished inside the fused launch (the last CTA runs the reduce
+of the tile partials, the length block, the tag and the verify gate)
+against the oracle, and the boundary to the separate combine kernel.
 
 A message of 1..1024 tiles and at most 2^22 blocks is finished by the last
 CTA to take a ticket; the ticket word (one per stream) wraps back to zero
