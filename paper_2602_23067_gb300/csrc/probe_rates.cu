@@ -315,6 +315,58 @@ int run_cycles(F launch, int sms, double *median_cycles)
     return 0;
 }
 
+// A 256-byte S-box held in registers across the warp: lane l keeps bytes
+// 8l..8l+7 in two words; looking up byte x fetches both words of lane x / 8
+// with two shuffles and selects byte x mod 8 with a byte permute.
+__device__ __forceinline__ uint32_t shfl_lookup(uint32_t x, uint32_t lo, uint32_t hi)
+{
+    const int src = (int)((x >> 3) & 31u);
+    const uint32_t a = __shfl_sync(0xFFFFFFFFu, lo, src);
+    const uint32_t b = __shfl_sync(0xFFFFFFFFu, hi, src);
+    return __byte_perm(a, b, x & 7u) & 0xFFu;
+}
+
+// MIX = 0: shuffle lookups alone (4 independent chains per thread).  MIX > 0:
+// every iteration is one AES-like round on the replicated round tables (16
+// shared lookups, as in lds32_kernel MODE 0) plus MIX shuffle lookups, to
+// see whether shuffles take capacity from the shared-memory pipe.
+template <int MIX>
+__global__ void shfl_kernel(int iters, uint32_t *sink, unsigned long long *cycles)
+{
+    extern __shared__ uint8_t tb[];
+    if (MIX > 0)
+        for (int i = threadIdx.x; i < 32768; i += blockDim.x)
+            reinterpret_cast<uint32_t *>(tb)[i] = (uint32_t)i * 2654435761u;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t lo = lane * 0x9E3779B9u, hi = lane * 0x7F4A7C15u;
+    const uint32_t cA = lane * 4u, cB = 128u + lane * 4u;
+    const uint8_t *t01 = tb, *t23 = tb + 65536;
+    uint32_t s0 = threadIdx.x * 0x9E3779B9u, s1 = s0 ^ 0x12345678u, s2 = s0 * 3u, s3 = ~s0;
+    const uint32_t k = 0x0F1E2D3Cu ^ blockIdx.x;
+    uint32_t x[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) x[c] = threadIdx.x * 7919u + 104729u * c;
+#define PL(t, w, B, c) (*reinterpret_cast<const uint32_t *>((t) + __byte_perm((w), (c), 0x5504u | ((B) << 4))))
+    const unsigned long long t0 = clock64();
+    for (int i = 0; i < iters; i++) {
+        if (MIX > 0) {
+            const uint32_t n0 = PL(t01, s0, 0, cA) ^ PL(t01, s1, 1, cB) ^ PL(t23, s2, 2, cA) ^ PL(t23, s3, 3, cB) ^ k;
+            const uint32_t n1 = PL(t01, s1, 0, cA) ^ PL(t01, s2, 1, cB) ^ PL(t23, s3, 2, cA) ^ PL(t23, s0, 3, cB) ^ k;
+            const uint32_t n2 = PL(t01, s2, 0, cA) ^ PL(t01, s3, 1, cB) ^ PL(t23, s0, 2, cA) ^ PL(t23, s1, 3, cB) ^ k;
+            const uint32_t n3 = PL(t01, s3, 0, cA) ^ PL(t01, s0, 1, cB) ^ PL(t23, s1, 2, cA) ^ PL(t23, s2, 3, cB) ^ k;
+            s0 = n0; s1 = n1; s2 = n2; s3 = n3;
+        }
+#pragma unroll
+        for (int c = 0; c < (MIX > 0 ? MIX : 4); c++) x[c & 3] = shfl_lookup(x[c & 3], lo, hi) + (x[c & 3] >> 8) + (uint32_t)i;
+    }
+#undef PL
+    __syncthreads();
+    const unsigned long long t1 = clock64();
+    if ((s0 ^ s1 ^ s2 ^ s3 ^ x[0] ^ x[1] ^ x[2] ^ x[3]) == 0x12345678u) sink[threadIdx.x] = s0;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -415,6 +467,35 @@ int probe_gather(int kind, int threads, int iters, double *lookups_per_clk_per_s
     if (rc) return rc;
     const double per_iter = (kind == 2) ? 8.0 * 9 : (kind == 3) ? 8.0 * 25 : 8.0;
     *lookups_per_clk_per_sm = (double)threads * iters * per_iter / cyc;
+    return 0;
+}
+
+// Warp-shuffle S-box lookups (two shuffles and a byte permute each):
+// out[0] shared-memory round-table lookups and out[1] shuffle lookups, per
+// clock per SM.  mix 0 runs shuffle lookups alone; mix 4, 8 or 16 adds that
+// many per AES-like round of 16 shared lookups.
+int probe_shfl(int mix, int threads, int iters, double out[2])
+{
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (sms > 1024 || threads <= 0 || threads > 1024 || (threads & 31) || iters <= 0) return -1;
+    if (mix != 0 && mix != 4 && mix != 8 && mix != 16) return -1;
+    const int smem32 = 131072;
+    CK(cudaFuncSetAttribute(shfl_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32));
+    CK(cudaFuncSetAttribute(shfl_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32));
+    CK(cudaFuncSetAttribute(shfl_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem32));
+    double cyc = 0;
+    auto launch = [&](uint32_t *sink, unsigned long long *c) {
+        if (mix == 0) shfl_kernel<0><<<sms, threads>>>(iters, sink, c);
+        else if (mix == 4) shfl_kernel<4><<<sms, threads, smem32>>>(iters, sink, c);
+        else if (mix == 8) shfl_kernel<8><<<sms, threads, smem32>>>(iters, sink, c);
+        else shfl_kernel<16><<<sms, threads, smem32>>>(iters, sink, c);
+    };
+    int rc = run_cycles(launch, sms, &cyc);
+    if (rc) return rc;
+    out[0] = mix ? (double)threads * iters * 16.0 / cyc : 0.0;
+    out[1] = (double)threads * iters * (mix ? mix : 4) / cyc;
     return 0;
 }
 

@@ -29,6 +29,7 @@ def _lib():
     L.probe_lds.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(d)]
     L.probe_gather.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(d)]
     L.probe_mma_b1.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(d)]
+    L.probe_shfl.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(d)]
     L.probe_host.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(d)]
     return L
 
@@ -56,6 +57,15 @@ def run(host_bytes: int = 4 << 30) -> dict:
     res["other_gather_paths"] = {
         "%s_%dthreads" % (name, t): _call(L, L.probe_gather, k, t, 1024)
         for k, name in enumerate(gk) for t in (512, 1024)}
+    sh = {}
+    for mix in (0, 4, 8, 16):
+        for t in (512, 1024):
+            o = (ctypes.c_double * 2)()
+            rc = L.probe_shfl(mix, t, 1024, o)
+            if rc != 0:
+                raise RuntimeError("probe_shfl failed: %d (line %d)" % (rc, L.probe_last_error_line()))
+            sh["mix%d_%dthreads" % (mix, t)] = {"shared_lookups": o[0], "shuffle_lookups": o[1]}
+    res["shuffle_sbox_lookups"] = sh
     res["mma_b1_m16n8k256"] = {
         "independent4_512threads": _call(L, L.probe_mma_b1, 4, 512, 256),
         "dependent_512threads": _call(L, L.probe_mma_b1, 1, 512, 256),
