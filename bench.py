@@ -155,14 +155,6 @@ def check_small(key, iv, aad, pt0, ct, tag):
         raise SystemExit("1 MiB message differs from the oracle")
 
 
-
-
-
-
-
-
-
-
 def run_reference(args):
     rank, local, world = dist_setup(args.gpus)
     if rank != 0:
@@ -505,18 +497,6 @@ def run_ours(args):
     return 0
 
 
-
-
-
-
-
-
-
-
-
-
-
-
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -531,9 +511,12 @@ def main():
     ap.add_argument("--catalog-pairs", type=int, default=683, help="catalog: float32/int16 file pairs (683 = 64 GiB)")
     ap.add_argument("--catalog-memory", choices=["pinned", "pageable"], default="pinned",
                     help="catalog: page-locked host memory (default) or ordinary pageable memory")
-    ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog"], default="fits4g",
+    ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog", "plan"],
+                    default="fits4g",
                     help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages; "
-                         "serving: Poisson request stream")
+                         "serving: Poisson request stream; plan: small batches, CUDA-graph plan vs gcm_batch vs "
+                         "one call per message")
+    ap.add_argument("--batch-sizes", default="1,16,128,1024", help="plan: messages per batch")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving arrival rates (req/s)")
     ap.add_argument("--seconds", type=float, default=3.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--max-requests", type=int, default=20000, help="serving: cap on requests per rate")
@@ -560,6 +543,8 @@ def main():
         return bw.run_serving(args)
     if args.workload == "catalog":
         return bw.run_catalog(args, cpu_baseline=cpu_catalog if cpu else None)
+    if args.workload == "plan":
+        return bw.run_plan(args)
     return run_ours(args)
 
 

@@ -54,7 +54,7 @@ typedef enum {
     GCM_ERR_CUDA = -5,          /* a CUDA runtime call failed */
     GCM_ERR_TIMEOUT = -6,       /* a bounded device-side wait gave up */
     GCM_ERR_ALIGNMENT = -7,     /* a device pt/ct pointer is not 16-byte aligned */
-    GCM_ERR_BUSY = -8           /* serving queue full; retry later */
+    GCM_ERR_BUSY = -8           /* serving queue full, or a run in flight; retry later */
 } gcm_status;
 
 /* Where the data buffers of a call live. */
@@ -270,6 +270,56 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
  * of n).  Used to measure per-message latency inside one persistent launch. */
 int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
                     int32_t *status, uint64_t *done_ns, void *stream);
+
+/* A device-memory batch prepared once and replayed as a CUDA graph.  The
+ * paper launches its kernels file by file (Sec. 3.3.2) and has no
+ * counterpart; a plan serves pipelines that run batches of one shape over
+ * and over (the same message lengths, new keys, IVs and data each time),
+ * where the per-call host work of gcm_batch -- validation, ordering,
+ * layout, scratch allocation, six enqueued operations and the
+ * synchronisation -- costs more than the device work of a small batch.
+ *
+ * gcm_batch_plan_create validates msgs exactly like gcm_batch in
+ * GCM_MEM_DEVICE mode (n >= 1), allocates the batch's scratch (device
+ * memory, counted against the context's HBM budget) and a page-locked
+ * image of its descriptors, and captures the whole run -- descriptor
+ * upload, counter reset, key setup for every message, the persistent
+ * (message, tile) kernel, for decrypt the zero-fill of failed messages, and
+ * the verdict download -- into one CUDA graph.  The plan copies the
+ * messages' keys and IVs; the device buffers (aad, in, out, tag) must stay
+ * valid while a run uses them.  *out receives the plan, or NULL on failure
+ * (GCM_ERR_INVALID_ARG, GCM_ERR_LENGTH_LIMIT, GCM_ERR_ALIGNMENT as for
+ * gcm_batch; GCM_ERR_NO_MEMORY; GCM_ERR_CUDA).  The plan belongs to ctx and
+ * must be destroyed before it.
+ *
+ * gcm_batch_plan_set replaces messages first .. first + count - 1 (the
+ * caller's indices at creation) by msgs[0 .. count - 1] for the following
+ * runs: any keys, IVs and device buffers, with the payload, AAD, key and IV
+ * lengths each message was created with.  All are checked before any is
+ * replaced (GCM_ERR_INVALID_ARG / GCM_ERR_ALIGNMENT otherwise, and nothing
+ * changes).  It may be called while a run is in flight.
+ *
+ * gcm_batch_plan_launch enqueues one run on `stream` (a cudaStream_t; NULL
+ * is the legacy default stream) and returns.  The first run, and every run
+ * after gcm_batch_plan_set changed a key, builds all messages' key material
+ * (round keys, powers of H, GHASH table); the other runs keep it and derive
+ * only each message's J0 and E_K(J0), as the server does for registered
+ * keys (a second captured graph).  gcm_batch_plan_wait waits for
+ * it and writes the per-message verdicts (0 or GCM_ERR_AUTH, the caller's
+ * order) to status (host array of n, may be NULL).  Runs of one plan share
+ * its scratch, so a plan has at most one run in flight: launch returns
+ * GCM_ERR_BUSY until the previous run has been waited for.  Results are
+ * those of gcm_batch on the same messages.  A plan is used by one thread at
+ * a time; different plans are independent. */
+typedef struct gcm_batch_plan gcm_batch_plan;
+int gcm_batch_plan_create(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
+                          gcm_batch_plan **out);
+int gcm_batch_plan_set(gcm_batch_plan *plan, size_t first, const gcm_msg *msgs, size_t count);
+int gcm_batch_plan_launch(gcm_batch_plan *plan, void *stream);
+int gcm_batch_plan_wait(gcm_batch_plan *plan, int32_t *status);
+/* Waits for a run in flight, then releases the plan's graph, scratch and
+ * descriptor image (cleared first: it holds the keys).  NULL is a no-op. */
+void gcm_batch_plan_destroy(gcm_batch_plan *plan);
 
 /* How host buffers (GCM_MEM_HOST, host batches, the server) reach the GPU.
  * mode 0 (default, auto): when the device can access host memory directly

@@ -11,7 +11,7 @@ from __future__ import annotations
 _API_NAMES = {
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
     "gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "last_error",
-    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server", "HostBuffer",
+    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server", "HostBuffer", "BatchPlan",
 }
 
 

@@ -128,6 +128,11 @@ SIGNATURES = {
     "gcm_noalloc_last_error": (ctypes.c_char_p, []),
     "gcm_host_alloc": (ctypes.c_int, [ctypes.c_int, _SZ, ctypes.POINTER(_VP)]),
     "gcm_host_free": (ctypes.c_int, [_VP]),
+    "gcm_batch_plan_create": (ctypes.c_int, [_VP, ctypes.POINTER(GcmMsg), _SZ, ctypes.c_int, ctypes.POINTER(_VP)]),
+    "gcm_batch_plan_set": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(GcmMsg), _SZ]),
+    "gcm_batch_plan_launch": (ctypes.c_int, [_VP, _VP]),
+    "gcm_batch_plan_wait": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int32)]),
+    "gcm_batch_plan_destroy": (None, [_VP]),
 }
 
 

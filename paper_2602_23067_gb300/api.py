@@ -17,7 +17,7 @@ from ._native import (GCM_ERR_AUTH, GCM_MEM_DEVICE, GCM_MEM_HOST, GCM_OK, GFC_AA
 __all__ = [
     "Context", "GcmError", "GCM_OK", "GCM_ERR_AUTH", "GCM_MEM_DEVICE", "GCM_MEM_HOST",
     "gcm_ctx_create", "gcm_ctx_destroy", "gcm_encrypt", "gcm_decrypt_verify", "last_error",
-    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server", "HostBuffer",
+    "FitsResult", "GFC_AAD_HEADER", "GFC_AAD_STRUCTURAL", "Server", "HostBuffer", "BatchPlan",
 ]
 
 
@@ -275,34 +275,22 @@ class Context:
         keep = []
         device = None
         for i, m in enumerate(msgs):
-            kp, kl, kk = _host_buf(m["key"])
-            ip, il, ik = _host_buf(m["iv"])
-            keep += [kk, ik]
             dev = hasattr(m["inp"], "is_cuda") and m["inp"].is_cuda
             if device is None:
                 device = dev
             elif device != dev:
                 raise ValueError("all messages of a batch must be in the same memory space")
-            if dev:
-                ap, al = _dev_buf(m.get("aad"))
-                pp, pl = _dev_buf(m["inp"])
-                op, ol = _dev_buf(m["out"])
-                tp, tl = _dev_buf(m["tag"])
-            else:
-                ap, al, ak = _host_buf(m.get("aad"))
-                pp, pl, pk = _host_buf(m["inp"])
-                op, ol, ok = _host_buf(m["out"])
-                tp, tl, tk = _host_buf(m["tag"])
-                keep += [ak, pk, ok, tk]
-            n_bytes = m.get("len", pl)
-            if ol < n_bytes or tl < 16:
-                raise ValueError("output or tag buffer too small")
-            arr[i] = GcmMsg(kp, kl, ip, il, ap or None, al, pp or None, op or None, n_bytes, tp)
+            arr[i] = _gcm_msg(m, dev, keep)
         status = (ctypes.c_int32 * max(1, n))()
         mem = GCM_MEM_DEVICE if device else GCM_MEM_HOST
         st = _stream_handle(stream) if device else 0
         check(lib.gcm_batch(self.handle, arr, n, 1 if decrypt else 0, status, mem, st))
         return [int(status[i]) for i in range(n)]
+
+    def batch_plan(self, msgs, decrypt: bool = False) -> "BatchPlan":
+        """gcm_batch_plan_create over device messages (dicts as for ``batch``):
+        the batch prepared once and replayed as a CUDA graph."""
+        return BatchPlan(self, msgs, decrypt)
 
     # -- key cache and serving ----------------------------------------------
     def key_register(self, key: bytes) -> int:
@@ -518,6 +506,82 @@ def _dev_tensor_copy(ptr: int, n: int, device):
     out = view.clone()
     torch.cuda.synchronize(device)
     return out
+
+
+def _gcm_msg(m, dev: bool, keep: list) -> GcmMsg:
+    """One gcm_msg from a dict with keys key, iv (bytes) and aad, inp, out,
+    tag (CUDA tensors when dev, else host buffers); optional len."""
+    kp, kl, kk = _host_buf(m["key"])
+    ip, il, ik = _host_buf(m["iv"])
+    keep += [kk, ik]
+    if dev:
+        ap, al = _dev_buf(m.get("aad"))
+        pp, pl = _dev_buf(m["inp"])
+        op, ol = _dev_buf(m["out"])
+        tp, tl = _dev_buf(m["tag"])
+    else:
+        ap, al, ak = _host_buf(m.get("aad"))
+        pp, pl, pk = _host_buf(m["inp"])
+        op, ol, ok = _host_buf(m["out"])
+        tp, tl, tk = _host_buf(m["tag"])
+        keep += [ak, pk, ok, tk]
+    n_bytes = m.get("len", pl)
+    if ol < n_bytes or tl < 16:
+        raise ValueError("output or tag buffer too small")
+    return GcmMsg(kp, kl, ip, il, ap or None, al, pp or None, op or None, n_bytes, tp)
+
+
+class BatchPlan:
+    """A device batch replayed as a CUDA graph (gcm_batch_plan_*): ``set``
+    swaps a message's key, IV and buffers (same lengths), ``launch`` enqueues
+    one run, ``wait`` returns its per-message statuses."""
+
+    def __init__(self, ctx: "Context", msgs, decrypt: bool):
+        self.ctx = ctx
+        self.n = len(msgs)
+        keep = []
+        arr = (GcmMsg * max(1, self.n))()
+        for i, m in enumerate(msgs):
+            if not (hasattr(m["inp"], "is_cuda") and m["inp"].is_cuda):
+                raise ValueError("a batch plan takes device (CUDA tensor) messages")
+            arr[i] = _gcm_msg(m, True, keep)
+        h = ctypes.c_void_p()
+        check(lib.gcm_batch_plan_create(ctx.handle, arr, self.n, 1 if decrypt else 0, ctypes.byref(h)))
+        self.handle = h.value
+        self._status = (ctypes.c_int32 * max(1, self.n))()
+
+    def set(self, i: int, msg) -> None:
+        self.set_many(i, [msg])
+
+    def set_many(self, first: int, msgs) -> None:
+        """Replaces messages first .. first + len(msgs) - 1 in one call."""
+        keep = []
+        arr = (GcmMsg * max(1, len(msgs)))()
+        for k, m in enumerate(msgs):
+            arr[k] = _gcm_msg(m, True, keep)
+        check(lib.gcm_batch_plan_set(self.handle, first, arr, len(msgs)))
+
+    def launch(self, stream=None) -> None:
+        check(lib.gcm_batch_plan_launch(self.handle, _stream_handle(stream)))
+
+    def wait(self):
+        check(lib.gcm_batch_plan_wait(self.handle, self._status))
+        return [int(self._status[i]) for i in range(self.n)]
+
+    def run(self, stream=None):
+        self.launch(stream)
+        return self.wait()
+
+    def close(self) -> None:
+        if self.handle:
+            lib.gcm_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Server:

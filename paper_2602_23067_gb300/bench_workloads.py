@@ -1,6 +1,6 @@
 """The secondary benchmark workloads (``bench.py --workload ...``): the
 10,000-message batch, the Poisson serving stream, the 64 GiB catalog in host
-memory and the single 1 MiB message.
+memory, the single 1 MiB message and small batches replayed as CUDA graphs.
 
 Each runner times the library's calls and prints one JSON line.  The CPU
 baselines (and the 1 MiB workload's check of message 0) are callables that
@@ -610,5 +610,180 @@ def run_small(args, cpu_baseline=None, check=None):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_plan(args):
+    """Small batches, where the host's work per batch is comparable to the
+    device's: for batches of B messages (lognormal lengths, median 16 KiB,
+    clipped 16 B..256 KiB, ~30% not multiples of 16, AES-128/256 mixed, 5%
+    non-96-bit IVs, AAD 0..4 KiB), the host latency from the first call to
+    the verdicts being on the host, of
+
+      * one gcm_encrypt call per message, then a stream synchronisation
+        (the key cache holds every key of the batch);
+      * one gcm_batch call (the persistent launch; returns with the verdicts);
+      * a batch plan: one gcm_batch_plan_set replacing all B messages (the
+        next window's buffers and IVs, the same keys: the key material is
+        kept), one graph launch, the wait;
+      * the same plan replayed without changes (the floor of a replay);
+      * the plan with other keys in every window (key setup in every run).
+
+    Every repetition takes the next of 8 windows of the input arena (other
+    buffers, other IVs), and L2 is flushed (a 256 MiB write) before each
+    repetition, outside the timed interval.  Calls go through the ctypes
+    binding with their argument arrays built beforehand."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2602_23067_gb300 import Context, _native, workloads
+
+    rank, local, world = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    ctx = Context(local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    lib = _native.lib
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sizes = [int(x) for x in args.batch_sizes.split(",")]
+    reps = max(20, args.steps)
+    W = 8
+    results = {}
+    launches = 0
+    _native.gcm_profile_read(ctx.handle, reset=True)
+    for B in sizes:
+        descs = workloads.message_mix(40 + B, B, median=16 << 10, sigma=1.0, lo=16, hi=256 << 10,
+                                      frac_unaligned=0.3, frac_long_iv=0.05, aad_max=4096, key_sizes=(16, 32))
+        lens = [d["len"] for d in descs]
+        aads = [d["aad_len"] for d in descs]
+        slot = [(n + 255) // 256 * 256 for n in lens]
+        offs = np.concatenate([[0], np.cumsum(slot)]).astype(np.int64)
+        aoffs = np.concatenate([[0], np.cumsum(aads)]).astype(np.int64)
+        win = int(offs[-1])
+        g = torch.Generator(device="cuda")
+        g.manual_seed(B)
+        arena_in = torch.randint(0, 256, (W * win,), dtype=torch.uint8, device="cuda", generator=g)
+        arena_out = torch.empty_like(arena_in)
+        aad_arena = torch.randint(0, 256, (max(1, W * int(aoffs[-1])),), dtype=torch.uint8, device="cuda",
+                                  generator=g)
+        tags = torch.empty(W * B * 16, dtype=torch.uint8, device="cuda")
+        r = workloads.rng(7 + B)
+        keep = []
+
+        def window_arrays(new_keys):
+            return [window_array(w, new_keys) for w in range(W)]
+
+        def window_array(w, new_keys):
+            arr = (_native.GcmMsg * B)()
+            for i, d in enumerate(descs):
+                key = r.integers(0, 256, len(d["key"]), dtype=np.uint8).tobytes() if new_keys else d["key"]
+                kb = ctypes.create_string_buffer(key, len(d["key"]))
+                ib = ctypes.create_string_buffer(r.integers(0, 256, len(d["iv"]), dtype=np.uint8).tobytes(),
+                                                 len(d["iv"]))
+                keep.extend([kb, ib])
+                a = aad_arena.data_ptr() + w * int(aoffs[-1]) + int(aoffs[i]) if aads[i] else None
+                arr[i] = _native.GcmMsg(ctypes.addressof(kb), len(d["key"]), ctypes.addressof(ib), len(d["iv"]),
+                                        a, aads[i], arena_in.data_ptr() + w * win + int(offs[i]),
+                                        arena_out.data_ptr() + w * win + int(offs[i]), lens[i],
+                                        tags.data_ptr() + 16 * (w * B + i))
+            return arr
+
+        arrays = window_arrays(False)  # the same keys in every window, other IVs
+        arrays_new_keys = window_arrays(True)  # other keys and IVs in every window
+        status = (ctypes.c_int32 * B)()
+
+        ctx.set_key_cache(max(64, B))  # every key of the batch stays set up for the per-message calls
+
+        def per_message(w):
+            for m in arrays[w]:
+                rc = lib.gcm_encrypt(ctx.handle, m.key, m.key_len, m.iv, m.iv_len, m.aad, m.aad_len, m.in_,
+                                     m.len, m.out, m.tag, 0, sh)
+                if rc:
+                    raise SystemExit("gcm_encrypt failed: %s" % _native.last_error())
+            stream.synchronize()
+
+        def batch(w):
+            if lib.gcm_batch(ctx.handle, arrays[w], B, 0, status, 0, sh):
+                raise SystemExit("gcm_batch failed: %s" % _native.last_error())
+
+        plan = ctypes.c_void_p()
+        if lib.gcm_batch_plan_create(ctx.handle, arrays[0], B, 0, ctypes.byref(plan)):
+            raise SystemExit("gcm_batch_plan_create failed: %s" % _native.last_error())
+
+        def plan_run(w, source=arrays):
+            if w is not None and lib.gcm_batch_plan_set(plan, 0, source[w], B):
+                raise SystemExit("gcm_batch_plan_set failed: %s" % _native.last_error())
+            if lib.gcm_batch_plan_launch(plan, sh) or lib.gcm_batch_plan_wait(plan, status):
+                raise SystemExit("batch plan run failed: %s" % _native.last_error())
+
+        # the three paths agree on every window (parity against the oracle is
+        # in the tests)
+        outs = []
+        for fn in (per_message, batch, plan_run):
+            arena_out.zero_()
+            tags.zero_()
+            for w in range(W):
+                fn(w)
+            torch.cuda.synchronize()
+            outs.append(torch.cat([arena_out, tags]).clone())
+        if not (torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])):
+            raise SystemExit("the batch paths disagree")
+        del outs
+
+        def timed(fn, replay=False):
+            lat = []
+            for k in range(reps + 3):
+                flush.fill_(k & 255)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                fn(None if replay else k % W)
+                dt = (time.perf_counter() - t0) * 1e3
+                if k >= 3:
+                    lat.append(dt)
+            return {"p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99), "mean_ms": statistics.mean(lat)}
+
+        res = {"per_message": timed(per_message), "gcm_batch": timed(batch), "plan": timed(plan_run),
+               "plan_replay_unchanged": timed(plan_run, replay=True),
+               "plan_new_keys_every_run": timed(lambda w: plan_run(w, arrays_new_keys))}
+        lib.gcm_batch_plan_destroy(plan)
+        payload = sum(lens)
+        for v in res.values():
+            v["gbs_at_p50"] = payload / (v["p50_ms"] * 1e-3) / 1e9
+        res["payload_bytes"] = payload
+        res["plan_speedup_p50"] = {"vs_gcm_batch": res["gcm_batch"]["p50_ms"] / res["plan"]["p50_ms"],
+                                   "vs_per_message": res["per_message"]["p50_ms"] / res["plan"]["p50_ms"]}
+        results[str(B)] = res
+        del arena_in, arena_out, aad_arena, tags
+        torch.cuda.empty_cache()
+    launches = _native.gcm_profile_read(ctx.handle, reset=True)["launches"]
+    ref_b = "128" if "128" in results else str(sizes[-1])
+    line = {
+        "metric": "small batches: host latency per batch (p50/p99), batch plan replayed as a CUDA graph vs "
+                  "gcm_batch vs one call per message",
+        "value": results[ref_b]["plan"]["p50_ms"],
+        "unit": "ms (p50, batch of %s messages, plan)" % ref_b,
+        "n_gpus": world,
+        "steps": reps,
+        "warmup": 3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "small_batches_lognormal16KiB", "batch_sizes": sizes,
+                   "lengths": "lognormal median 16 KiB sigma 1.0 clipped 16 B..256 KiB, 30% not multiples of 16",
+                   "keys": "AES-128/AES-256 50/50", "ivs": "96-bit, 5% 8..128 bytes", "aad": "0..4 KiB",
+                   "l2": "256 MiB write before every repetition, outside the timed interval",
+                   "host": "ctypes binding, argument arrays built beforehand; encrypt direction"},
+        "batches": results,
+        "gpu_launches": launches,
+        "e2e": None,
+        "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     ctx.close()
     return 0

@@ -102,3 +102,19 @@ def test_header_is_plain_c_and_links(native, tmp_path):
     # The boundary needs no C++ and no Python: a C99 program that includes
     # the header compiles without warnings and links against the library.
     assert os.path.exists(build_c_consumer(str(tmp_path)))
+
+
+def test_batch_plan_argument_errors(native):
+    # The plan calls check their handles before any CUDA call.
+    import ctypes
+
+    out = ctypes.c_void_p(1)
+    msg = native.GcmMsg()
+    rc = native.lib.gcm_batch_plan_create(None, ctypes.byref(msg), 1, 0, ctypes.byref(out))
+    assert rc == native.GCM_ERR_INVALID_ARG
+    assert out.value is None
+    assert native.lib.gcm_batch_plan_create(None, ctypes.byref(msg), 1, 0, None) == native.GCM_ERR_INVALID_ARG
+    assert native.lib.gcm_batch_plan_set(None, 0, ctypes.byref(msg), 1) == native.GCM_ERR_INVALID_ARG
+    assert native.lib.gcm_batch_plan_launch(None, None) == native.GCM_ERR_INVALID_ARG
+    assert native.lib.gcm_batch_plan_wait(None, None) == native.GCM_ERR_INVALID_ARG
+    native.lib.gcm_batch_plan_destroy(None)
