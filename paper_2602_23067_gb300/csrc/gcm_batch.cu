@@ -59,6 +59,7 @@ int check_device_msg(const gcm_msg &m)
 // Everything below host_bytes is the descriptor image filled on the host.
 struct BatchLayout {
     size_t n = 0;
+    uint32_t tile_log2 = BATCH_TILE_LOG2;  // tile size of every message of the batch
     std::vector<size_t> order;  // slot -> caller's index
     std::vector<uint64_t> K, base, o_km, o_part, o_tree, o_iv;
     uint64_t items = 0;
@@ -68,7 +69,8 @@ struct BatchLayout {
 
 namespace {
 
-void make_layout(const gcm_msg *msgs, size_t n, BatchLayout &L)
+// tile_log2: the batch's tile size, forced (9..16) or 0 for the rule below.
+void make_layout(const gcm_msg *msgs, size_t n, int num_sms, int tile_log2, BatchLayout &L)
 {
     L.n = n;
     // Work items go out shortest message first: slot j of the launch holds
@@ -81,6 +83,14 @@ void make_layout(const gcm_msg *msgs, size_t n, BatchLayout &L)
     std::iota(L.order.begin(), L.order.end(), (size_t)0);
     std::stable_sort(L.order.begin(), L.order.end(), [&](size_t a, size_t b) { return Mlen[a] < Mlen[b]; });
 
+    // Tiles: the largest size (2^9..2^16 blocks) that still gives every SM
+    // four tiles' worth of the batch's blocks, so that a batch of short
+    // messages spreads over the SMs (a message shorter than a tile would
+    // otherwise run on one SM) and large batches keep the largest tiles.
+    uint64_t total = 0;
+    for (size_t i = 0; i < n; i++) total += Mlen[i];
+    L.tile_log2 = tile_log2 ? (uint32_t)tile_log2 : choose_tile_log2(total, num_sms);
+    const uint32_t lg = L.tile_log2;
     L.K.assign(n, 0);
     L.base.assign(n, 0);
     L.o_km.assign(n, 0);
@@ -90,7 +100,7 @@ void make_layout(const gcm_msg *msgs, size_t n, BatchLayout &L)
     L.items = 0;
     for (size_t j = 0; j < n; j++) {
         const uint64_t M = Mlen[L.order[j]];
-        uint64_t k = (M + (1ull << BATCH_TILE_LOG2) - 1) >> BATCH_TILE_LOG2;
+        uint64_t k = (M + (1ull << lg) - 1) >> lg;
         if (k == 0) k = 1;  // an empty message still has one (empty) tile, so its tag gets computed
         L.K[j] = k;
         L.base[j] = L.items;
@@ -145,6 +155,7 @@ void fill_slot(const BatchLayout &L, size_t j, const gcm_msg &m, bool decrypt, b
     b.item_base = L.base[j];
     b.nr = (uint32_t)m.key_len / 4 + 6;
     b.dec = decrypt ? 1u : 0u;
+    b.tile_log2 = L.tile_log2;
     b.km = reinterpret_cast<KeyMat *>(dev + L.o_km[j]);
     b.mm = reinterpret_cast<MsgMat *>(dev + L.o_km[j] + sizeof(KeyMat));
     b.partials = reinterpret_cast<gf128 *>(dev + L.o_part[j]);
@@ -239,7 +250,7 @@ int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int3
     } restore{prev};
 
     BatchLayout L;
-    make_layout(msgs, n, L);
+    make_layout(msgs, n, ctx->num_sms, ctx->forced_tile_log2, L);
     if (ctx->budget && L.total > ctx->budget)
         return ctx_fail(GCM_ERR_NO_MEMORY, "batch scratch would exceed the context's HBM budget");
 
@@ -366,7 +377,7 @@ int gcm_batch_plan_create(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decry
     P->ctx = ctx;
     P->device = ctx->device;
     P->decrypt = decrypt != 0;
-    make_layout(msgs, n, P->L);
+    make_layout(msgs, n, ctx->num_sms, ctx->forced_tile_log2, P->L);
     const BatchLayout &L = P->L;
     if (ctx->budget && L.total > ctx->budget) {
         plan_free(P);

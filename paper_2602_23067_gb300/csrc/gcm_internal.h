@@ -20,7 +20,7 @@ constexpr int GH_LOG2_STRIDE = 5;
 constexpr int SEGF_MIN_LOG2 = 9;   // smallest tile: 2^9 blocks (32 per warp)
 constexpr int SEGF_SIZES = 8;      // tile sizes 2^9 .. 2^16
 constexpr int H2K_COUNT = 40;  // H^(2^k), k = 0..39 (covers 2^39 blocks)
-constexpr uint32_t BATCH_TILE_LOG2 = 16;  // tile size of the batched kernel (2^16 blocks)
+constexpr uint32_t BATCH_TILE_LOG2 = 16;  // largest tile of the batched kernel (2^16 blocks)
 constexpr int GTAB_ENTRIES = 4096;  // 256 byte values x 16 byte positions
 // Warps of the fused kernel that run their GHASH chains through the integer
 // field multiply instead of the table (a measured alternative; 0 = none).
@@ -140,10 +140,11 @@ struct BatchMsg {
     const uint8_t *aad;
     uint64_t len;
     uint64_t aad_len;
-    uint64_t K;             // tiles of 2^BATCH_TILE_LOG2 blocks
+    uint64_t K;             // tiles of 2^tile_log2 blocks
     uint64_t item_base;     // index of the message's first work item
     uint32_t nr;
     uint32_t dec;           // 1: decrypt-verify this message (GHASH over the input)
+    uint32_t tile_log2;     // SEGF_MIN_LOG2 .. BATCH_TILE_LOG2
     KeyMat *km;
     MsgMat *mm;
     gf128 *partials;        // K entries

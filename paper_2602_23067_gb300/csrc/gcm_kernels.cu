@@ -1179,7 +1179,7 @@ __device__ void batch_combine(uint8_t *smem, const BatchMsg &m, bool dec)
     bool reversed = true;
     while (cnt > 1) {
         const uint64_t half = (cnt + 1) / 2;
-        const gf128 mult = m.km->h2k[BATCH_TILE_LOG2 + level];
+        const gf128 mult = m.km->h2k[m.tile_log2 + level];
         const bool by_warp = half <= (uint64_t)nwarps * 4;
         const uint64_t first = by_warp ? (uint64_t)warp : (uint64_t)t;
         const uint64_t step = by_warp ? (uint64_t)nwarps : (uint64_t)blockDim.x;
@@ -1287,7 +1287,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         v.n_full = bm.len / 16;
         v.M = v.a_blocks + (bm.len + 15) / 16;
         v.K = bm.K;
-        v.tile_log2 = BATCH_TILE_LOG2;
+        v.tile_log2 = bm.tile_log2;
         v.dec = bm.dec != 0;
         v.km = bm.km;
         v.mm = bm.mm;
@@ -1297,7 +1297,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
             stage_ghash_table(smem, bm.km);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             if (lane == 0)
-                reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[BATCH_TILE_LOG2 - SEGF_MIN_LOG2][warp];
+                reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[bm.tile_log2 - SEGF_MIN_LOG2][warp];
             cur = mi;
             gc.grp = gc.grp_hi = 0xFFFFFFFFu;  // the constants belong to the previous message
             __syncthreads();

@@ -198,6 +198,7 @@ int launch_wave(gcm_server *S, Wave &w)
         }
         b.len = r.len;
         b.aad_len = r.aad_len;
+        b.tile_log2 = BATCH_TILE_LOG2;  // the tile count the admission budgeted for
         b.K = K[i];
         b.item_base = base[i];
         b.nr = ctx->key_nr[r.key];

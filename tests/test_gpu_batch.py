@@ -165,3 +165,50 @@ def test_host_mode_single_message_many_chunks(env, host_access):
         assert back.tobytes() == pt
     finally:
         c2.close()
+
+
+@pytest.mark.parametrize("lg", [9, 10, 11, 12, 13, 14, 15, 16])
+def test_batch_at_every_tile_size(env, lg):
+    """A batch's tiles are 2^lg blocks for all its messages (by default the
+    largest size that gives every SM four tiles of the batch; forced here):
+    encryption and decrypt-verify (one tampered tag) against the oracle at
+    every size, with a message spanning 2..129 tiles."""
+    torch, ctx = env
+    msgs = make_mix(33 + lg, 12, median=30000, sigma=1.5, hi=600000)
+    msgs.append({"key": bytes(range(16)), "iv": bytes(range(12)), "aad": b"a" * 50,
+                 "pt": workloads.random_bytes(90 + lg, (1 << 20) + 9).tobytes()})
+    enc = [oracle.gcm_encrypt(m["key"], m["iv"], m["aad"], m["pt"]) for m in msgs]
+    dm = []
+    for m in msgs:
+        dm.append({"key": m["key"], "iv": m["iv"], "aad": dev(torch, m["aad"])[: len(m["aad"])] if m["aad"] else None,
+                   "inp": dev(torch, m["pt"]), "out": torch.empty(max(1, len(m["pt"])), dtype=torch.uint8,
+                                                                  device="cuda"),
+                   "tag": torch.empty(16, dtype=torch.uint8, device="cuda"), "len": len(m["pt"])})
+    ctx.set_tile_log2(lg)
+    try:
+        assert ctx.batch(dm) == [0] * len(msgs)
+        torch.cuda.synchronize()
+        for d, m, (ref_ct, ref_tag) in zip(dm, msgs, enc):
+            assert bytes(d["tag"].cpu().numpy()) == ref_tag
+            assert bytes(d["out"][: len(m["pt"])].cpu().numpy()) == ref_ct
+        bad = len(msgs) - 1
+        back = []
+        for i, (d, m) in enumerate(zip(dm, msgs)):
+            t = bytearray(enc[i][1])
+            if i == bad:
+                t[3] ^= 4
+            back.append({"key": m["key"], "iv": m["iv"], "aad": d["aad"], "inp": d["out"],
+                         "out": torch.full((max(1, len(m["pt"])),), 0x5A, dtype=torch.uint8, device="cuda"),
+                         "tag": dev(torch, bytes(t)), "len": len(m["pt"])})
+        st = ctx.batch(back, decrypt=True)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_tile_log2(0)
+    for i, (b, m) in enumerate(zip(back, msgs)):
+        got = bytes(b["out"][: len(m["pt"])].cpu().numpy())
+        if i == bad:
+            assert st[i] == -3
+            assert got == bytes(len(m["pt"]))
+        else:
+            assert st[i] == 0
+            assert got == m["pt"]
