@@ -108,11 +108,12 @@ bool is_direct(const gcm_server *S, const gcm_request &r)
 // device reaches host memory directly and the payload is 16-byte aligned).
 bool is_direct(const gcm_server *S, const gcm_request &r);
 
-// Device bytes a request needs inside a wave arena.
+// Device bytes a request needs inside a wave arena, at most: its tile
+// partials are counted at the smallest tile a wave may choose.
 size_t request_bytes(const gcm_server *S, const gcm_request &r)
 {
     const uint64_t M = (r.aad_len + 15) / 16 + (r.len + 15) / 16;
-    uint64_t K = (M + (1ull << BATCH_TILE_LOG2) - 1) >> BATCH_TILE_LOG2;
+    uint64_t K = (M + (1ull << SEGF_MIN_LOG2) - 1) >> SEGF_MIN_LOG2;
     if (K == 0) K = 1;
     const size_t data = is_direct(S, r) ? 0 : al(r.len) + al(r.aad_len);
     return data + al(sizeof(MsgMat)) + al(K * sizeof(gf128)) + al((K / 2 + 1) * sizeof(gf128)) +
@@ -149,11 +150,16 @@ int launch_wave(gcm_server *S, Wave &w)
     const size_t zero_bytes = off - o_done;
     std::vector<size_t> o_mm(n), o_part(n), o_tree(n), o_pay(n), o_aad(n);
     std::vector<uint64_t> K(n), base(n);
+    // One tile size for the wave: the largest that gives every SM four tiles'
+    // worth of its blocks, so a light wave spreads over the SMs.
+    uint64_t total = 0;
+    for (size_t i = 0; i < n; i++) total += (w.reqs[i].r.aad_len + 15) / 16 + (w.reqs[i].r.len + 15) / 16;
+    const uint32_t lg = ctx->forced_tile_log2 ? (uint32_t)ctx->forced_tile_log2 : choose_tile_log2(total, ctx->num_sms);
     uint64_t items = 0;
     for (size_t i = 0; i < n; i++) {
         const gcm_request &r = w.reqs[i].r;
         const uint64_t M = (r.aad_len + 15) / 16 + (r.len + 15) / 16;
-        uint64_t k = (M + (1ull << BATCH_TILE_LOG2) - 1) >> BATCH_TILE_LOG2;
+        uint64_t k = (M + (1ull << lg) - 1) >> lg;
         if (k == 0) k = 1;
         K[i] = k;
         base[i] = items;
@@ -198,7 +204,7 @@ int launch_wave(gcm_server *S, Wave &w)
         }
         b.len = r.len;
         b.aad_len = r.aad_len;
-        b.tile_log2 = BATCH_TILE_LOG2;  // the tile count the admission budgeted for
+        b.tile_log2 = lg;
         b.K = K[i];
         b.item_base = base[i];
         b.nr = ctx->key_nr[r.key];
