@@ -283,8 +283,9 @@ int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
  *
  * gcm_batch_plan_create validates msgs exactly like gcm_batch in
  * GCM_MEM_DEVICE mode (n >= 1), allocates the batch's scratch (device
- * memory, counted against the context's HBM budget) and a page-locked
- * image of its descriptors, and captures the whole run -- descriptor
+ * memory held until the plan is destroyed and counted against the context's
+ * HBM budget meanwhile, like the scratch of calls in flight) and a
+ * page-locked image of its descriptors, and captures the whole run -- descriptor
  * upload, counter reset, key setup for every message, the persistent
  * (message, tile) kernel, for decrypt the zero-fill of failed messages, and
  * the verdict download -- into one CUDA graph.  The plan copies the

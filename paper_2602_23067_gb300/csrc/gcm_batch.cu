@@ -305,6 +305,7 @@ struct gcm_batch_plan {
     std::vector<size_t> slot_of;  // caller's index -> slot
     std::vector<gcm_msg> shape;   // lengths fixed at creation (caller's order; pointers unused)
     uint8_t *dev = nullptr;       // scratch, held until destroy
+    size_t held = 0;              // bytes of it counted in the context's scratch in flight
     uint8_t *pinned = nullptr;    // descriptor image read by every replay, then the verdict words
     int32_t *hstat = nullptr;
     std::vector<uint8_t> pending;  // descriptor image edited by gcm_batch_plan_set
@@ -347,6 +348,10 @@ void plan_free(gcm_batch_plan *P)
     }
     if (P->done) cudaEventDestroy(P->done);
     if (P->dev) cudaFree(P->dev);
+    if (P->held) {
+        std::lock_guard<std::mutex> lk(P->ctx->mu);
+        P->ctx->in_flight -= P->held;
+    }
     if (P->pinned) {
         memset(P->pinned, 0, P->L.host_bytes);  // the image holds the keys
         cudaFreeHost(P->pinned);
@@ -379,9 +384,17 @@ int gcm_batch_plan_create(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decry
     P->decrypt = decrypt != 0;
     make_layout(msgs, n, ctx->num_sms, ctx->forced_tile_log2, P->L);
     const BatchLayout &L = P->L;
-    if (ctx->budget && L.total > ctx->budget) {
+    {
+        // Held for the plan's lifetime, like the scratch of calls in flight.
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        if (!ctx->budget || ctx->in_flight + L.total <= ctx->budget) {
+            ctx->in_flight += L.total;
+            P->held = L.total;
+        }
+    }
+    if (!P->held) {
         plan_free(P);
-        return ctx_fail(GCM_ERR_NO_MEMORY, "batch scratch would exceed the context's HBM budget");
+        return ctx_fail(GCM_ERR_NO_MEMORY, "the plan's scratch would exceed the context's HBM budget");
     }
     P->shape.assign(msgs, msgs + n);
     P->slot_of.assign(n, 0);

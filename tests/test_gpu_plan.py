@@ -213,3 +213,29 @@ def test_plan_contract(env):
         # the rejected updates changed nothing
         assert plan.run() == [0, 0]
         check_against_oracle(bufs, data)
+
+
+def test_plan_scratch_counts_against_the_budget(env):
+    """A plan holds its scratch (one message: ~70 KB, mostly the key
+    material) until it is destroyed, counted in the context's HBM budget: with
+    a 120 KB budget a second plan is refused until the first is gone."""
+    torch, _ = env
+    from paper_2602_23067_gb300 import Context, GcmError
+    from paper_2602_23067_gb300 import _native as nat
+
+    shp = [{"len": 4000, "key_len": 32, "iv_len": 12, "aad_len": 16}]
+    bufs = device_msgs(torch, shp)
+    data = contents(11, shp)
+    load(torch, bufs, data)
+    torch.cuda.synchronize()
+    msgs = [as_msg(b, d) for b, d in zip(bufs, data)]
+    with Context(0, hbm_budget_bytes=120_000) as ctx:
+        first = ctx.batch_plan(msgs)
+        with pytest.raises(GcmError) as e:
+            ctx.batch_plan(msgs)
+        assert e.value.code == nat.GCM_ERR_NO_MEMORY
+        assert first.run() == [0]
+        first.close()
+        with ctx.batch_plan(msgs) as second:
+            assert second.run() == [0]
+    check_against_oracle(bufs, data)
