@@ -446,12 +446,20 @@ def run_ours(args):
                         "binding pipe (AES round-table and GHASH-table lookups)",
                 "sms": sms, "sm_mhz": mhz, "sm_mhz_source": "median sampled during the timed region"}
         if counters is not None and mhz:
-            wpb, cmd = counters
+            wpb = counters["wavefronts"]
             payload_peak = sms * mhz * 1e6 / wpb * 16.0 / 1e9
             pipe_peak = payload_peak * kern_bytes / padded  # in algorithmic bytes, like `achieved`
-            pipe.update({"wavefronts_per_block": wpb, "wavefronts_source": "ncu, profiles/fused_traffic.json: " + cmd,
+            pipe.update({"wavefronts_per_block": wpb,
+                         "wavefronts_source": "ncu, profiles/fused_traffic.json: " + counters["command"],
                          "peak_payload_gbs": payload_peak, "peak_gbs_algorithmic": pipe_peak,
                          "frac": achieved / pipe_peak})
+            if counters["warp_instructions"]:
+                # The issue bound beside it: 4 warp instructions per clock per
+                # SM over the measured warp instructions per block.
+                wi = counters["warp_instructions"]
+                issue_payload = sms * 4 * mhz * 1e6 / wi * 16.0 / 1e9
+                pipe["issue_bound"] = {"warp_instructions_per_block": wi, "peak_payload_gbs": issue_payload,
+                                       "frac": achieved / (issue_payload * kern_bytes / padded)}
         else:
             pipe.update({"wavefronts_per_block": None, "frac": None,
                          "note": "no ncu wavefront count for the current kernel source" if counters is None

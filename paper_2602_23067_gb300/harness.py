@@ -80,16 +80,19 @@ def load_traffic():
 
 
 def load_pipe_counters():
-    """Shared-memory (LSU) data-pipe wavefronts per 16-byte block of the fused
-    kernel (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared over the blocks of
-    one launch), from the committed capture, if it was taken on the current
-    kernel source; else None."""
+    """Per 16-byte block of the fused kernel, from the committed capture if it
+    was taken on the current kernel source (else None): shared-memory (LSU)
+    data-pipe wavefronts (ncu l1tex__data_pipe_lsu_wavefronts_mem_shared) and
+    warp instructions (smsp__inst_executed), each over the blocks of one
+    launch, with the capture's command."""
     p = os.path.join(ROOT, "profiles", "fused_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
         if d.get("source_sha256") == kernel_source_hash() and d.get("lsu_wavefronts_per_block"):
-            return float(d["lsu_wavefronts_per_block"]), d.get("command", "")
+            wi = d.get("warp_instructions_per_block")
+            return {"wavefronts": float(d["lsu_wavefronts_per_block"]),
+                    "warp_instructions": float(wi) if wi else None, "command": d.get("command", "")}
     except Exception:
         pass
     return None

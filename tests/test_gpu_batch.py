@@ -212,3 +212,70 @@ def test_batch_at_every_tile_size(env, lg):
         else:
             assert st[i] == 0
             assert got == m["pt"]
+
+
+def _wrap_iv(key, nblocks, r):
+    """A 16-byte IV whose J0 has a low word within nblocks - 100 of 2^32, so
+    that inc32 wraps inside a message of nblocks blocks (searched with the
+    oracle's J0)."""
+    import ctypes
+
+    h, _, _ = oracle.h_j0(key, bytes(12))
+    hb = ctypes.create_string_buffer(h, 16)
+    out = ctypes.create_string_buffer(16)
+    for _ in range(1 << 24):
+        iv = bytes(r.randrange(256) for _ in range(16))
+        ivb = ctypes.create_string_buffer(iv, 16)
+        oracle.lib().oracle_j0(ctypes.addressof(hb), ctypes.addressof(ivb), 16, ctypes.addressof(out))
+        if int.from_bytes(out.raw[12:16], "big") >= (1 << 32) - nblocks + 100:
+            return iv
+    raise AssertionError("no wrapping IV found")
+
+
+@pytest.mark.parametrize("lg", [0, 16])
+def test_batch_with_one_byte_iv_and_counter_wrap(env, lg):
+    """Batch members on the GHASH(IV) path: a 1-byte IV (outside what other
+    libraries accept) and a 16-byte IV whose counter wraps mod 2^32 inside
+    the message, among ordinary ones; encrypt (gcm_batch and a batch plan)
+    and decrypt-verify against the oracle, at the batch's own tile size and
+    at 2^16-block tiles."""
+    torch, ctx = env
+    r = random.Random(6000 + lg)
+    wrap_key = bytes(r.randrange(256) for _ in range(32))
+    nwrap = 1 << 16
+    msgs = [
+        {"key": bytes(r.randrange(256) for _ in range(16)), "iv": bytes([r.randrange(256)]), "aad": b"x" * 21,
+         "pt": workloads.random_bytes(6001, 50007).tobytes()},
+        {"key": wrap_key, "iv": _wrap_iv(wrap_key, nwrap, r), "aad": b"", "pt": workloads.random_bytes(
+            6002, 16 * nwrap - 3).tobytes()},
+    ] + make_mix(6003, 4, median=20000, sigma=1.0, hi=200000)
+    enc = [oracle.gcm_encrypt(m["key"], m["iv"], m["aad"], m["pt"]) for m in msgs]
+
+    def dmsgs(src, dst, tags):
+        return [{"key": m["key"], "iv": m["iv"], "aad": dev(torch, m["aad"])[: len(m["aad"])] if m["aad"] else None,
+                 "inp": s, "out": d, "tag": t, "len": len(m["pt"])} for m, s, d, t in zip(msgs, src, dst, tags)]
+
+    src = [dev(torch, m["pt"]) for m in msgs]
+    outs = [torch.empty(max(1, len(m["pt"])), dtype=torch.uint8, device="cuda") for m in msgs]
+    tags = [torch.empty(16, dtype=torch.uint8, device="cuda") for _ in msgs]
+    ctx.set_tile_log2(lg)
+    try:
+        assert ctx.batch(dmsgs(src, outs, tags)) == [0] * len(msgs)
+        torch.cuda.synchronize()
+        for m, o, t, (ref_ct, ref_tag) in zip(msgs, outs, tags, enc):
+            assert bytes(t.cpu().numpy()) == ref_tag
+            assert bytes(o[: len(m["pt"])].cpu().numpy()) == ref_ct
+        outs2 = [torch.zeros_like(o) for o in outs]
+        tags2 = [torch.zeros_like(t) for t in tags]
+        with ctx.batch_plan(dmsgs(src, outs2, tags2)) as plan:
+            assert plan.run() == [0] * len(msgs)
+        for m, o, t, (ref_ct, ref_tag) in zip(msgs, outs2, tags2, enc):
+            assert bytes(t.cpu().numpy()) == ref_tag
+            assert bytes(o[: len(m["pt"])].cpu().numpy()) == ref_ct
+        back = [torch.zeros_like(o) for o in outs]
+        assert ctx.batch(dmsgs(outs, back, tags), decrypt=True) == [0] * len(msgs)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_tile_log2(0)
+    for m, b in zip(msgs, back):
+        assert bytes(b[: len(m["pt"])].cpu().numpy()) == m["pt"]
