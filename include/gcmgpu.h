@@ -139,9 +139,10 @@ int gcm_ctx_set_key_cache(gcm_ctx *ctx, size_t entries);
  * default t comes from the context's tuning table (on a GB300 with 152 SMs a
  * table measured there with gcm_ctx_autotune is installed at creation),
  * else from a rule (t = 16, lowered down to 9 while there are fewer than 4
- * tiles per SM).  A device-memory batch (gcm_batch, batch plans; also a
- * host-memory batch the kernels run on directly) uses one t for all its
- * messages, from the same rule over the batch's total blocks.
+ * tiles per SM).  A batch (gcm_batch, a batch plan, a server wave) uses one
+ * t for all its messages, from the batch's total blocks: in device memory
+ * the t that balances a tile's fixed work against the tail of the last
+ * tiles, for host memory and the server the rule above.
  * gcm_ctx_set_tile_log2 forces t = tile_log2 (9..16) for every call and
  * every batch or plan created afterwards; 0 returns to the default. */
 int gcm_ctx_set_tile_log2(gcm_ctx *ctx, int tile_log2);

@@ -786,7 +786,7 @@ int gcm_batch(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt, int32_t 
                 }
                 s = ctx->s_comp;
             }
-            return batch_device(ctx, msgs, n, decrypt != 0, status, nullptr, s);
+            return batch_device(ctx, msgs, n, decrypt != 0, status, nullptr, s, true);
         }
         return stream_host(ctx, msgs, n, decrypt != 0, status);
     }

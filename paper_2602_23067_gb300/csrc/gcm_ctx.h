@@ -116,7 +116,8 @@ cudaEvent_t ctx_take_event(gcm_ctx *ctx);
 int stream_host(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status);
 void stream_release(gcm_ctx *ctx);
 // Device-memory messages in one persistent batched launch (gcm_batch.cu).
+// host_mem: the buffers are host memory the kernels reach directly.
 int batch_device(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, bool decrypt, int32_t *status, uint64_t *done_ns,
-                 cudaStream_t s);
+                 cudaStream_t s, bool host_mem = false);
 }  // namespace gcmgpu
 
