@@ -276,25 +276,26 @@ int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
 
 /* A device-memory batch prepared once and replayed as a CUDA graph.  The
  * paper launches its kernels file by file (Sec. 3.3.2) and has no
- * counterpart; a plan serves pipelines that run batches of one shape over
- * and over (the same message lengths, new keys, IVs and data each time),
- * where the per-call host work of gcm_batch -- validation, ordering,
- * layout, scratch allocation, six enqueued operations and the
- * synchronisation -- costs more than the device work of a small batch.
+ * counterpart.  A plan serves pipelines that run batches of one shape over
+ * and over (the same message lengths, new IVs and data each time, the same
+ * or new keys).  It does gcm_batch's per-call host work (validation,
+ * ordering, layout, scratch allocation, the enqueued operations) once, and
+ * keeps the key material between runs whose keys do not change.
  *
  * gcm_batch_plan_create validates msgs exactly like gcm_batch in
- * GCM_MEM_DEVICE mode (n >= 1), allocates the batch's scratch (device
- * memory held until the plan is destroyed and counted against the context's
- * HBM budget meanwhile, like the scratch of calls in flight) and a
- * page-locked image of its descriptors, and captures the whole run -- descriptor
- * upload, counter reset, key setup for every message, the persistent
- * (message, tile) kernel, for decrypt the zero-fill of failed messages, and
- * the verdict download -- into one CUDA graph.  The plan copies the
- * messages' keys and IVs; the device buffers (aad, in, out, tag) must stay
- * valid while a run uses them.  *out receives the plan, or NULL on failure
- * (GCM_ERR_INVALID_ARG, GCM_ERR_LENGTH_LIMIT, GCM_ERR_ALIGNMENT as for
- * gcm_batch; GCM_ERR_NO_MEMORY; GCM_ERR_CUDA).  The plan belongs to ctx and
- * must be destroyed before it.
+ * GCM_MEM_DEVICE mode (n >= 1).  It allocates the batch's scratch (device
+ * memory, held until the plan is destroyed and counted against the
+ * context's HBM budget meanwhile, like the scratch of calls in flight) and
+ * a page-locked image of its descriptors.  It captures the whole run into
+ * a CUDA graph: descriptor upload, counter reset, key setup for every
+ * message, the persistent (message, tile) kernel, for decrypt the zero-fill
+ * of failed messages, and the verdict download.  A second graph is the same
+ * run with the key setup replaced by the per-message J0 / E_K(J0) step.
+ * The plan copies the messages' keys and IVs; the device buffers (aad, in,
+ * out, tag) must stay valid while a run uses them.  *out receives the plan,
+ * or NULL on failure (GCM_ERR_INVALID_ARG, GCM_ERR_LENGTH_LIMIT,
+ * GCM_ERR_ALIGNMENT as for gcm_batch; GCM_ERR_NO_MEMORY; GCM_ERR_CUDA).
+ * The plan belongs to ctx and must be destroyed before it.
  *
  * gcm_batch_plan_set replaces messages first .. first + count - 1 (the
  * caller's indices at creation) by msgs[0 .. count - 1] for the following
@@ -305,10 +306,11 @@ int gcm_batch_timed(gcm_ctx *ctx, const gcm_msg *msgs, size_t n, int decrypt,
  *
  * gcm_batch_plan_launch enqueues one run on `stream` (a cudaStream_t; NULL
  * is the legacy default stream) and returns.  The first run, and every run
- * after gcm_batch_plan_set changed a key, builds all messages' key material
- * (round keys, powers of H, GHASH table); the other runs keep it and derive
+ * after gcm_batch_plan_set changed a key, replays the first graph and builds
+ * all messages' key material (round keys, powers of H, GHASH table).  The
+ * other runs replay the second graph: they keep that material and derive
  * only each message's J0 and E_K(J0), as the server does for registered
- * keys (a second captured graph).  gcm_batch_plan_wait waits for
+ * keys.  gcm_batch_plan_wait waits for
  * it and writes the per-message verdicts (0 or GCM_ERR_AUTH, the caller's
  * order) to status (host array of n, may be NULL).  Runs of one plan share
  * its scratch, so a plan has at most one run in flight: launch returns
