@@ -106,6 +106,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
                                MsgMat *mm, const DevTables *tabs, KeyFin *fin = nullptr)
 {
     __shared__ uint8_t sbox[256];
+    __shared__ uint32_t stt[4 * 256];  // T0..T3: the two single-block AES calls read them here
     __shared__ uint32_t rkw[60];
     __shared__ gf128 sH;
     __shared__ gf128 sh2k[H2K_COUNT];
@@ -114,12 +115,14 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
     const int t = threadIdx.x;
 
     sbox[t] = tabs->sbox[t];
+#pragma unroll
+    for (int r = 0; r < 4; r++) stt[r * 256 + t] = tabs->ttab[r * 256 + t];
     __syncthreads();
     if (t == 0) {
         int nr = key_expand_words(key, (int)key_len, sbox, rkw);
         s_nr = nr;
         uint32_t zero[4] = {0u, 0u, 0u, 0u}, h[4];
-        aes_block_tt(rkw, nr, tabs->ttab, tabs->sbox, zero, h);
+        aes_block_tt(rkw, nr, stt, sbox, zero, h);
         sH = gf_from_mem(h[0], h[1], h[2], h[3]);
     }
     __syncthreads();
@@ -159,7 +162,7 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
             j0[0] = jm.x; j0[1] = jm.y; j0[2] = jm.z; j0[3] = jm.w;
         }
         uint32_t e[4];
-        aes_block_tt(rkw, nr, tabs->ttab, tabs->sbox, j0, e);
+        aes_block_tt(rkw, nr, stt, sbox, j0, e);
         for (int i = 0; i < 4; i++) {
             mm->j0[i] = j0[i];
             mm->ej0[i] = e[i];
@@ -210,17 +213,20 @@ __device__ void key_setup_body(const uint8_t *key, uint32_t key_len, const uint8
         }
     }
     __syncthreads();
-    // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32.
-    // Bit b of v (LSB = 0) is the coefficient of x^(8k + 7 - b).
+    // 8-bit table: entry (v, k) = (byte value v at byte position k) * H^32,
+    // stored at v * 16 + k.  Bit b of v (LSB = 0) is the coefficient of
+    // x^(8k + 7 - b).  The lanes of a warp share k, so their basis reads are
+    // broadcasts (lanes on different k would read entries 128 bytes apart,
+    // all in one bank group).
     for (int idx = t; idx < GTAB_ENTRIES; idx += blockDim.x) {
-        const int v = idx >> 4, k = idx & 15;
+        const int k = idx >> 8, v = idx & 255;
         gf128 acc = gf_zero();
         for (int b = 0; b < 8; b++) {
             const uint32_t m = 0u - (uint32_t)((v >> b) & 1);
             const gf128 &bv = basis[8 * k + 7 - b];
             for (int i = 0; i < 4; i++) acc.w[i] ^= bv.w[i] & m;
         }
-        km->gtab[idx] = gf_to_mem(acc);
+        km->gtab[v * 16 + k] = gf_to_mem(acc);
     }
 }
 
