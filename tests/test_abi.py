@@ -118,3 +118,16 @@ def test_batch_plan_argument_errors(native):
     assert native.lib.gcm_batch_plan_launch(None, None) == native.GCM_ERR_INVALID_ARG
     assert native.lib.gcm_batch_plan_wait(None, None) == native.GCM_ERR_INVALID_ARG
     native.lib.gcm_batch_plan_destroy(None)
+
+
+def test_batch_plan_binding_takes_device_tensors_only(native):
+    # The binding refuses host buffers before it calls the library (a plan
+    # is a device-memory batch).
+    torch = pytest.importorskip("torch")
+    from paper_2602_23067_gb300.api import BatchPlan
+
+    host = torch.zeros(32, dtype=torch.uint8)
+    msg = {"key": bytes(16), "iv": bytes(12), "aad": None, "inp": host, "out": host,
+           "tag": torch.zeros(16, dtype=torch.uint8)}
+    with pytest.raises(ValueError):
+        BatchPlan(None, [msg], False)
