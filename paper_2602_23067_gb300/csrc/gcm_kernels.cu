@@ -473,6 +473,22 @@ __device__ __forceinline__ void stage_ghash_table(uint8_t *smem, const KeyMat *k
     for (int i = threadIdx.x; i < GTAB_ENTRIES; i += blockDim.x) sg[i] = __ldg(&g[i]);
 }
 
+// The same for a block of NT threads with every load of a thread in flight
+// before its first store: one memory round trip per staging instead of one
+// per entry (the batched kernel restages at every change of message).
+template <int NT>
+__device__ __forceinline__ void stage_ghash_table_in_flight(uint8_t *smem, const KeyMat *km)
+{
+    constexpr int GT = GTAB_ENTRIES / NT;
+    const uint4 *g = km->gtab;
+    uint4 *sg = reinterpret_cast<uint4 *>(smem + SM_GTAB);
+    uint4 e[GT];
+#pragma unroll
+    for (int k = 0; k < GT; k++) e[k] = __ldg(&g[threadIdx.x + k * NT]);
+#pragma unroll
+    for (int k = 0; k < GT; k++) sg[threadIdx.x + k * NT] = e[k];
+}
+
 // Both tables of the fused kernel (KF_THREADS threads), with every global
 // load of a thread issued before its first shared-memory store, so that the
 // staging costs about one memory round trip instead of one per loop trip.
@@ -1300,7 +1316,7 @@ __global__ void __launch_bounds__(KF_THREADS, 1) batch_kernel(const __grid_const
         v.partials = bm.partials;
         if (mi != cur) {
             // New message: its key's GHASH table and segment factors.
-            stage_ghash_table(smem, bm.km);
+            stage_ghash_table_in_flight<KF_THREADS>(smem, bm.km);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             if (lane == 0)
                 reinterpret_cast<gf128 *>(smem + SM_SEGF)[warp] = bm.km->segf[bm.tile_log2 - SEGF_MIN_LOG2][warp];
