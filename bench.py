@@ -519,11 +519,11 @@ def main():
     ap.add_argument("--catalog-pairs", type=int, default=683, help="catalog: float32/int16 file pairs (683 = 64 GiB)")
     ap.add_argument("--catalog-memory", choices=["pinned", "pageable"], default="pinned",
                     help="catalog: page-locked host memory (default) or ordinary pageable memory")
-    ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog", "plan"],
+    ap.add_argument("--workload", choices=["fits4g", "small", "batched", "serving", "catalog", "plan", "plan-tiles"],
                     default="fits4g",
                     help="fits4g (default): one 4 GiB FITS file; batched: 10,000 independent messages; "
                          "serving: Poisson request stream; plan: small batches, CUDA-graph plan vs gcm_batch vs "
-                         "one call per message")
+                         "one call per message; plan-tiles: the same at every forced batch tile size")
     ap.add_argument("--batch-sizes", default="1,16,128,1024", help="plan: messages per batch")
     ap.add_argument("--rates", default="1000,2000,5000,10000,20000,50000", help="serving arrival rates (req/s)")
     ap.add_argument("--seconds", type=float, default=3.0, help="serving: seconds of arrivals per rate")
@@ -553,6 +553,8 @@ def main():
         return bw.run_catalog(args, cpu_baseline=cpu_catalog if cpu else None)
     if args.workload == "plan":
         return bw.run_plan(args)
+    if args.workload == "plan-tiles":
+        return bw.run_plan_tiles(args)
     return run_ours(args)
 
 

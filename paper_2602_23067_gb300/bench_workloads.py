@@ -787,3 +787,99 @@ def run_plan(args):
         print(json.dumps(line), flush=True)
     ctx.close()
     return 0
+
+
+def run_plan_tiles(args):
+    """The tile size of a device-memory batch, swept: for batches of B small
+    messages (the mix of ``run_plan``), plan replays with the same keys at
+    every forced tile size 2^9..2^16 (``gcm_ctx_set_tile_log2``), host
+    latency p50 / p99 per run (L2 flushed before each, outside the timed
+    interval), beside the size the library's own rule picks."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_2602_23067_gb300 import Context, _native, workloads
+
+    rank, local, world = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    ctx = Context(local)
+    lib = _native.lib
+    sh = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    sizes = [int(x) for x in args.batch_sizes.split(",")]
+    reps = max(20, args.steps)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    results = {}
+    for B in sizes:
+        descs = workloads.message_mix(40 + B, B, median=16 << 10, sigma=1.0, lo=16, hi=256 << 10,
+                                      frac_unaligned=0.3, frac_long_iv=0.05, aad_max=4096, key_sizes=(16, 32))
+        lens = [d["len"] for d in descs]
+        aads = [d["aad_len"] for d in descs]
+        offs = np.concatenate([[0], np.cumsum([(n + 255) // 256 * 256 for n in lens])]).astype(np.int64)
+        aoffs = np.concatenate([[0], np.cumsum(aads)]).astype(np.int64)
+        arena_in = torch.randint(0, 256, (int(offs[-1]),), dtype=torch.uint8, device="cuda")
+        arena_out = torch.empty_like(arena_in)
+        aad_arena = torch.randint(0, 256, (max(1, int(aoffs[-1])),), dtype=torch.uint8, device="cuda")
+        tags = torch.empty(B * 16, dtype=torch.uint8, device="cuda")
+        keep = []
+        arr = (_native.GcmMsg * B)()
+        for i, d in enumerate(descs):
+            kb = ctypes.create_string_buffer(d["key"], len(d["key"]))
+            ib = ctypes.create_string_buffer(d["iv"], len(d["iv"]))
+            keep.extend([kb, ib])
+            a = aad_arena.data_ptr() + int(aoffs[i]) if aads[i] else None
+            arr[i] = _native.GcmMsg(ctypes.addressof(kb), len(d["key"]), ctypes.addressof(ib), len(d["iv"]), a,
+                                    aads[i], arena_in.data_ptr() + int(offs[i]), arena_out.data_ptr() + int(offs[i]),
+                                    lens[i], tags.data_ptr() + 16 * i)
+        status = (ctypes.c_int32 * B)()
+        blocks = sum((n + 15) // 16 + (a + 15) // 16 for n, a in zip(lens, aads))
+        ref, sweep = None, {}
+        for lg in range(9, 17):
+            ctx.set_tile_log2(lg)
+            plan = ctypes.c_void_p()
+            rc = lib.gcm_batch_plan_create(ctx.handle, arr, B, 0, ctypes.byref(plan))
+            ctx.set_tile_log2(0)
+            if rc:
+                raise SystemExit("gcm_batch_plan_create failed: %s" % _native.last_error())
+            lat = []
+            for k in range(reps + 3):
+                flush.fill_(k & 255)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                if (lib.gcm_batch_plan_set(plan, 0, arr, B) or lib.gcm_batch_plan_launch(plan, sh)
+                        or lib.gcm_batch_plan_wait(plan, status)):
+                    raise SystemExit("batch plan run failed: %s" % _native.last_error())
+                if k >= 3:
+                    lat.append((time.perf_counter() - t0) * 1e6)
+            torch.cuda.synchronize()
+            lib.gcm_batch_plan_destroy(plan)
+            out = torch.cat([arena_out, tags]).clone()
+            if ref is None:
+                ref = out
+            elif not torch.equal(ref, out):  # every tile size gives the same bytes
+                raise SystemExit("tile size %d changed the result" % lg)
+            sweep[str(lg)] = {"p50_us": percentile(lat, 0.5), "p99_us": percentile(lat, 0.99)}
+        rule = min(16, max(9, round(0.5 * math.log2(max(1.0, blocks / sms) * 2400.0))))
+        results[str(B)] = {"blocks_per_sm": blocks / sms, "rule_tile_log2": rule, "sweep": sweep}
+        del arena_in, arena_out, aad_arena, tags
+        torch.cuda.empty_cache()
+    line = {
+        "metric": "batch tile size sweep: host latency per plan run (p50/p99) at every forced tile size",
+        "value": None,
+        "unit": "us",
+        "n_gpus": world,
+        "steps": reps,
+        "warmup": 3,
+        "higher_is_better": False,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "small_batches_lognormal16KiB_tile_sweep", "batch_sizes": sizes,
+                   "l2": "256 MiB write before every repetition, outside the timed interval"},
+        "batches": results,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0

@@ -76,7 +76,7 @@ namespace {
 // against the tail of the last tiles, sqrt(blocks per SM x 2,400), rounded
 // to a power of two in 2^9..2^16.  Fitted on batches of 16, 128 and 1024
 // small messages: the fastest forced size at 16 and 1024 messages, within
-// 10% of it at 128; 2^16 for the 10,000-message mix.
+// 8-10% of it at 128; 2^16 for the 10,000-message mix.
 uint32_t device_batch_tile_log2(uint64_t total_blocks, int num_sms)
 {
     const double w = (double)total_blocks / (double)(num_sms > 0 ? num_sms : 1);
